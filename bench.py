@@ -1,0 +1,377 @@
+"""Benchmark: robust value iteration throughput (transition-updates/s) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+A step is one full finite-horizon query (K = 200 Bellman iterations, maximum
+pessimistic reachability, as in the paper's Sec. 5 experiments) over one batch
+of synthetic IMDPs already resident in HBM.  The metric is
+    transition-updates/s = (stored transitions) x (iterations) / time,
+summed over all ranks.  Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "transition-updates/s (robust Bellman, O-maximization), max-pessimistic finite reachability K=200"
+UNIT = "transition-updates/s"
+PAPER_PIMDP2_RATE = 48106480 * 200 / 30.0  # Sec. 5: pimdp_2, 200 steps, 30 s on a GTX1060
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name: str, rank: int, models: int = 0):
+    from workloads import make_config
+    from workloads.imdp_synth import CONFIGS
+    c = dict(CONFIGS[name])
+    kw = dict(seed=c["seed"] + 1000 * rank)
+    if models and c["kind"] == "batch":
+        kw["n_models"] = models
+    return make_config(name, **kw)
+
+
+def workload_config(name: str, m, horizon: int):
+    from workloads.imdp_synth import CONFIGS
+    c = dict(CONFIGS[name])
+    if m.model_state_offsets is not None:
+        c["n_models"] = len(m.model_state_offsets) - 1
+    cfg = {"workload": name, "states": int(m.n_states), "columns": int(m.n_cols), "transitions": int(m.nnz),
+           "horizon": horizon, "query": "maximize pessimistic reachability, finite horizon",
+           "models": int(c.get("n_models", 1)), "l2": "inputs larger than L2 (%.2f GB resident model)" %
+           (m.nnz * 20 / 1e9), "parallelism": "replicas"}
+    return cfg
+
+
+def algorithmic_bytes_per_iteration(m) -> int:
+    # rowval + lower + gap per transition; colptr + rem per column; stateptr + V read + V write per state
+    return 20 * int(m.nnz) + 12 * int(m.n_cols) + 20 * int(m.n_states)
+
+
+def bellman_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("bellman.cu", "imdp_internal.h"):
+        with open(os.path.join(ROOT, "paper_2401_04068_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """Per-launch DRAM bytes of the Bellman kernel from a committed ncu summary,
+    only if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "bellman_step_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    rec = d.get(workload)
+    if not rec or rec.get("source_hash") != bellman_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(m, horizon: int, budget_s: float = 12.0, sample_models: int = None):
+    """The oracle as it stands, on host cores, over a bounded sample of the workload."""
+    import oracle
+    from workloads import concat_block_diagonal  # noqa: F401
+    cores = os.cpu_count() or 1
+    offs = m.model_state_offsets if m.model_state_offsets is not None else np.array([0, m.n_states])
+    n_models = len(offs) - 1
+
+    def sub(nm):
+        # first nm models of the block-diagonal batch (or a prefix of one model's iterations)
+        s_end = int(offs[nm])
+        c_end = int(m.stateptr[s_end])
+        e_end = int(m.colptr[c_end])
+        return oracle.OracleIMDP(s_end, m.stateptr[:s_end + 1], m.colptr[:c_end + 1], m.rowval[:e_end],
+                                 m.lower[:e_end], m.upper[:e_end]), e_end
+
+    if n_models > 1:
+        # calibrate on one model, then size the sample to the budget
+        om1, nz1 = sub(1)
+        goal1 = m.goal[m.goal < offs[1]]
+        t = time.perf_counter()
+        oracle.value_iteration(om1, oracle.OracleSpec(horizon=horizon, reach=goal1), threads=cores)
+        dt = max(time.perf_counter() - t, 1e-4)
+        nm = sample_models or int(max(1, min(n_models, budget_s / dt)))
+        om, nz = sub(nm)
+        goal = m.goal[m.goal < offs[nm]]
+        iters = horizon
+        sample = f"first {nm} of {n_models} models, K={iters}"
+    else:
+        om, nz = sub(1)
+        goal = m.goal
+        t = time.perf_counter()
+        oracle.value_iteration(om, oracle.OracleSpec(horizon=1, reach=goal), threads=cores)
+        dt = max(time.perf_counter() - t, 1e-4)
+        iters = int(max(1, min(horizon, budget_s / dt)))
+        sample = f"whole model, K={iters} of {horizon} iterations (cost per iteration is constant)"
+    t = time.perf_counter()
+    st, V, k, _, _ = oracle.value_iteration(om, oracle.OracleSpec(horizon=iters, reach=goal), threads=cores)
+    el = time.perf_counter() - t
+    return {"value": nz * iters / el, "unit": UNIT, "cores": cores if oracle.has_openmp() else 1, "kind": "oracle",
+            "sample": sample, "seconds": round(el, 3)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle on a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    m = make_workload(args.workload, 0, args.models)
+    cfg = workload_config(args.workload, m, args.horizon)
+    per = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(m, args.horizon, budget_s=args.ref_budget)
+        if i >= args.warmup:
+            per.append(r["value"])
+            base = r
+    value = float(statistics.median(per)) if per else 0.0
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+           "cpu_baseline": dict(base, value=value) if base else None,
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2401_04068_gb300 as g
+    from paper_2401_04068_gb300 import build as pbuild
+
+    torch.cuda.set_device(local_rank)
+    if not os.path.exists(pbuild.LIB) or not pbuild.up_to_date():
+        if rank == 0 or world == 1:
+            pbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    g.load()
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+
+    m = make_workload(args.workload, rank, args.models)
+    model = g.create_model(m, stream=stream)
+    spec = g.make_spec(horizon=args.horizon, reach=m.goal, pessimistic=True, maximize=True)
+    sess = g.imdp_session_create([model], [spec], stream=stream)
+
+    def one_step(ev=None):
+        g.imdp_session_reset(sess, stream)
+        if ev is not None:
+            ev[0].record(stream)
+        g.imdp_session_step(sess, args.horizon, stream)
+        if ev is not None:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    # correctness guard on the timed configuration: the run must reach K
+    kk = [0]
+    Vd = torch.empty(m.n_states, dtype=torch.float64, device=dev)
+    g.imdp_session_read(sess, 0, Vd, kk, stream=stream)
+    assert kk[0] == args.horizon
+
+    launches0 = g.imdp_session_launches(sess)
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start.record(stream)
+    for i in range(args.steps):
+        one_step(kev[i])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    kernel_ms = sum(a.elapsed_time(b) for a, b in kev)
+    launches = g.imdp_session_launches(sess) - launches0
+    my_units = float(m.nnz) * args.horizon * args.steps
+    if world > 1:
+        t = torch.tensor([elapsed_ms, kernel_ms, my_units], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        torch.distributed.all_reduce(mx[:2], op=torch.distributed.ReduceOp.MAX)
+        sm = t.clone()
+        torch.distributed.all_reduce(sm[2:], op=torch.distributed.ReduceOp.SUM)
+        elapsed_ms, kernel_ms, total_units = float(mx[0]), float(mx[1]), float(sm[2])
+    else:
+        total_units = my_units
+    value = total_units / (elapsed_ms / 1e3)
+
+    # e2e: through the public C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(m, k))).pin_memory()
+               for k in ("stateptr", "colptr", "rowval", "lower", "upper")}
+        Vh = torch.empty(m.n_states, dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in pin.values())
+        d2h = Vh.numel() * Vh.element_size()
+
+        def e2e_step():
+            mdl = g.imdp_create_csc(m.n_states, m.n_cols, m.nnz, pin["stateptr"], pin["colptr"], pin["rowval"],
+                                    pin["lower"], pin["upper"], stream=stream)
+            kk2 = [0]
+            g.imdp_value_iteration(mdl, spec, Vh, kk2, stream=stream)
+            mdl.close()
+            return kk2[0]
+
+        e2e_step()  # warm-up
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            assert e2e_step() == args.horizon
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t[0])
+        e2e = {"value": float(m.nnz) * args.horizon * args.e2e_steps * world / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps}
+
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peak_hbm()
+    alg_bytes = algorithmic_bytes_per_iteration(m)
+    launch_ms = kernel_ms / (args.steps * args.horizon)
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    traffic = recorded_traffic(args.workload)
+    cfg = workload_config(args.workload, m, args.horizon)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": (value / world / PAPER_PIMDP2_RATE) if args.workload == "pimdp2" else None,
+        "dtype": "u64", "data": "synthetic (seeded banded IMDPs shaped like the paper's benchmark table)",
+        "config": cfg,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": peak_kind, "kernel": "bellman_step_kernel",
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": launch_ms},
+        "clocks": clk,
+        "gpu_launches": int(launches + args.steps),  # Bellman steps + one value-reset kernel per step
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(m, args.horizon, budget_s=args.ref_budget)
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pendulum240_x4096")
+    ap.add_argument("--horizon", type=int, default=200)
+    ap.add_argument("--models", type=int, default=0, help="override the number of models of a batch workload")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--ref-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * imdp.h — C ABI of the GB300 robust value-iteration library for Interval
+ * Markov Decision Processes (IMDPs), after arXiv 2401.04068 (IntervalMDP.jl).
+ *
+ * Model (Sec. 2): M = (S, A, P_up, P_lo). For every state-action pair (s, a)
+ * the transition probability to s' lies in [P_lo(s,a,s'), P_up(s,a,s')], with
+ * sum P_lo <= 1 <= sum P_up. Gamma_{s,a} is the set of feasible distributions.
+ *
+ * Storage (Sec. 3.1 and Sec. 5: compressed sparse column, source/action/
+ * destination indices stored sequentially): one CSC matrix whose columns are
+ * the (state, action) pairs of all states in order and whose rows are the
+ * destination states; `stateptr` maps each state to its range of columns
+ * (Appendix A lists the same arrays: colptr, rowval, nzval, stateptr).
+ * All indices are 0-based (the paper's Julia is 1-based).
+ *
+ * Computation (Eq. 2 / Eq. 3): robust value iteration
+ *   V_0 = 1_G,  V_k(s) = 1_G(s) + 1_{S\G}(s) opt^pi_a opt^eta_{p in Gamma_{s,a}} sum_s' V_{k-1}(s') p(s'),
+ * with the inner problem solved by O-maximization (Sec. 4).
+ *
+ * Conventions for every entry point:
+ *   - Errors are returned as imdp_status; nothing is thrown across the ABI.
+ *     imdp_last_error() gives a one-line detail for the calling thread.
+ *   - The caller owns every pointer it passes; the library copies what it keeps.
+ *   - "host or device" pointers are told apart with cudaPointerGetAttributes;
+ *     device pointers must be on the current CUDA device.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Every call
+ *     returns after its results are written (it synchronizes the stream).
+ *   - Outputs are written only when the call returns IMDP_OK (or IMDP_ENOCONV
+ *     for V/k/residual of an infinite horizon that hit its iteration cap).
+ *   - The library never falls back to the CPU: without a usable CUDA device
+ *     every compute call returns IMDP_EDEVICE.
+ */
+#ifndef IMDP_H
+#define IMDP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define IMDP_API __attribute__((visibility("default")))
+#else
+#define IMDP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IMDP_OK = 0,
+  IMDP_EINVAL = 1,       /* malformed arguments or CSC structure */
+  IMDP_EINFEASIBLE = 2,  /* some column violates 0 <= lo <= up <= 1, sum lo <= 1 <= sum up (Sec. 2) */
+  IMDP_ENOMEM = 3,       /* device or host allocation failed, or the server's HBM budget is too small */
+  IMDP_EDEVICE = 4,      /* CUDA error or no CUDA device */
+  IMDP_ETIMEOUT = 5,     /* a bounded device-side or host-side wait gave up */
+  IMDP_EBUSY = 6,        /* the server has no free slot; retry later */
+  IMDP_ENOCONV = 7,      /* infinite horizon: residual still >= eps at the iteration cap */
+  IMDP_ENOTFOUND = 8,    /* unknown server ticket */
+  IMDP_EPENDING = 9      /* server ticket not finished yet */
+} imdp_status;
+
+/* Storage precision of the transition bounds. IMDP_F64 keeps 64 bits per bound
+ * (stored as unsigned fixed point with 63 fractional bits, which resolves
+ * probabilities in [0, 1] to 1.1e-19 absolute, finer than binary64 near 1). */
+typedef enum { IMDP_F64 = 0, IMDP_F32 = 1 } imdp_dtype;
+
+/* Property types of the specification JSON schema (Appendix A). */
+typedef enum { IMDP_REACH = 0, IMDP_REACH_AVOID = 1, IMDP_REWARD = 2 } imdp_property;
+
+/* Specification (Sec. 3.2 and Appendix A): property, horizon, and the
+ * satisfaction (adversary) and strategy modes. All pointers are host pointers. */
+typedef struct {
+  int32_t property;      /* imdp_property */
+  int32_t infinite_time; /* 0: fixed horizon `horizon` (FiniteTime*); 1: iterate until max|V_k - V_{k-1}| < eps */
+  int32_t horizon;       /* K >= 0 for a finite horizon; iteration cap for an infinite one (0 = 1,000,000) */
+  double eps;            /* convergence tolerance on the maximum Bellman residual (infinite_time only) */
+  int32_t pessimistic;   /* 1: opt^eta = min (pessimistic); 0: opt^eta = max (optimistic) */
+  int32_t maximize;      /* 1: opt^pi = max; 0: opt^pi = min */
+  const int32_t* reach;  int32_t n_reach;  /* target set G (reach / reach-avoid) */
+  const int32_t* avoid;  int32_t n_avoid;  /* avoid set (reach-avoid); must not meet G */
+  const double* reward;  /* n_states rewards (reward property) */
+  double discount;       /* reward property: (0, 1] finite horizon, (0, 1) infinite */
+} imdp_spec;
+
+typedef struct imdp_model imdp_model;
+
+/* Human-readable name of a status code (static storage). */
+IMDP_API const char* imdp_status_string(imdp_status s);
+
+/* One-line detail of the last error raised on the calling thread ("" if none). */
+IMDP_API const char* imdp_last_error(void);
+
+/* Library version as "major.minor.patch" (static storage). */
+IMDP_API const char* imdp_version(void);
+
+/*
+ * Create a device-resident model from CSC arrays (Sec. 3.1, Appendix A).
+ *   n_states       |S| >= 1
+ *   n_cols         number of (state, action) columns, >= n_states
+ *   nnz            number of stored transitions, 0 <= nnz < 2^31
+ *   stateptr       int32[n_states + 1]: columns of state s are [stateptr[s], stateptr[s+1]);
+ *                  stateptr[0] = 0, strictly increasing (every state has >= 1 action),
+ *                  stateptr[n_states] = n_cols
+ *   colptr         int32[n_cols + 1]: entries of column j are [colptr[j], colptr[j+1]);
+ *                  colptr[0] = 0, nondecreasing, colptr[n_cols] = nnz
+ *   rowval         int32[nnz]: destination states, strictly increasing within a column
+ *   lower, upper   double[nnz]: P_lo and P_up of each stored transition
+ *   dtype          storage precision (IMDP_F64; IMDP_F32 halves the bound storage)
+ *   stream         cudaStream_t used for the upload and checks
+ *   out            receives the model handle (freed with imdp_model_destroy)
+ * Inputs may be host or device pointers; they are copied. Returns IMDP_EINVAL for
+ * broken structure, IMDP_EINFEASIBLE when a column is infeasible beyond an
+ * absolute tolerance of 1e-12 on the sums.
+ */
+IMDP_API imdp_status imdp_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, const int32_t* stateptr,
+                            const int32_t* colptr, const int32_t* rowval, const double* lower,
+                            const double* upper, imdp_dtype dtype, void* stream, imdp_model** out);
+
+/*
+ * Create a model from dense bounds (Sec. 3.1: IntervalProbabilities with rows =
+ * destination states and columns = actions, concatenated over source states).
+ *   n_actions      int32[n_states]: number of actions of each state (>= 1)
+ *   lower, upper   double[n_states * n_cols], column-major (entry (s', j) at j*n_states + s'),
+ *                  n_cols = sum n_actions. Entries with upper == 0 (and lower == 0) are
+ *                  structural zeros and are not stored. Host pointers only.
+ */
+IMDP_API imdp_status imdp_create_dense(int32_t n_states, const int32_t* n_actions, const double* lower,
+                              const double* upper, imdp_dtype dtype, void* stream, imdp_model** out);
+
+/* Free a model and its device memory. NULL is ignored. */
+IMDP_API void imdp_model_destroy(imdp_model* m);
+
+/* Model dimensions and the device bytes it holds. Any output may be NULL. */
+IMDP_API imdp_status imdp_model_info(const imdp_model* m, int32_t* n_states, int32_t* n_cols, int64_t* nnz,
+                            size_t* device_bytes, int32_t* max_col_nnz);
+
+/*
+ * value_iteration / control_synthesis (Sec. 3.2) on one model.
+ *   V_out         double[n_states] (host or device): V_k after the last iteration
+ *   k_out         (host, nullable) iterations performed
+ *   residual_out  double[n_states] (host or device, nullable): V_k - V_{k-1} state-wise
+ *   policy_out    int32 (host or device, nullable): finite horizon K x n_states,
+ *                 entry [t * n_states + s] = local action index for state s at time t
+ *                 (time 0 is the first step, the argmax of iteration K - t);
+ *                 infinite horizon n_states (stationary policy of the last iteration).
+ *                 States held fixed by the property (reach / avoid targets) get -1.
+ *                 Ties between actions go to the lowest local index.
+ */
+IMDP_API imdp_status imdp_value_iteration(imdp_model* m, const imdp_spec* spec, double* V_out, int32_t* k_out,
+                                 double* residual_out, int32_t* policy_out, void* stream);
+
+/*
+ * Run `count` independent problems (models[i], specs[i]) together: every
+ * Bellman iteration of every problem that is still running is one kernel
+ * launch for the whole batch. Results are identical to running each problem
+ * alone (integer accumulation; no cross-problem reduction).
+ *   V_out[i]   double[n_states of models[i]] (host or device)
+ *   k_out      int32[count] (host, nullable)
+ * A model may appear more than once (e.g. with different specs).
+ */
+IMDP_API imdp_status imdp_value_iteration_batch(imdp_model* const* models, const imdp_spec* specs, int32_t count,
+                                       double* const* V_out, int32_t* k_out, void* stream);
+
+/*
+ * Resident solver session: the device state of value iteration for `count`
+ * problems kept between calls (value buffers, iteration counters, policy
+ * storage), so repeated runs and step-by-step control need no re-setup.
+ * imdp_value_iteration(_batch) is create + step-until-done + read + destroy.
+ *   want_policy   int32[count] (nullable): 1 to record the policy of problem i
+ * The models must outlive the session. Sessions are not thread-safe.
+ */
+typedef struct imdp_session imdp_session;
+
+IMDP_API imdp_status imdp_session_create(imdp_model* const* models, const imdp_spec* specs, int32_t count,
+                                         const int32_t* want_policy, void* stream, imdp_session** out);
+
+/* Reset every problem to V_0 and iteration 0 (asynchronous on `stream`). */
+IMDP_API imdp_status imdp_session_reset(imdp_session* s, void* stream);
+
+/* Launch `n_iters` Bellman iterations (one kernel each; problems that are done
+ * or past their horizon are skipped on the device). Asynchronous on `stream`;
+ * chunks of iterations are replayed from a captured CUDA graph when `stream`
+ * is not the legacy default stream. */
+IMDP_API imdp_status imdp_session_step(imdp_session* s, int32_t n_iters, void* stream);
+
+/* Run until every problem is done (finite: its horizon; infinite: residual < eps
+ * or the cap), checking completion every `check_every` iterations (<= 0: 32). */
+IMDP_API imdp_status imdp_session_run(imdp_session* s, int32_t check_every, void* stream);
+
+/* Read problem `index`: outputs as in imdp_value_iteration; any may be NULL.
+ * Synchronizes `stream`. Returns IMDP_ENOCONV if that problem hit its cap. */
+IMDP_API imdp_status imdp_session_read(imdp_session* s, int32_t index, double* V_out, int32_t* k_out,
+                                       double* residual_out, int32_t* policy_out, void* stream);
+
+/* Number of step-kernel launches issued by the session so far. */
+IMDP_API int64_t imdp_session_launches(const imdp_session* s);
+
+IMDP_API void imdp_session_destroy(imdp_session* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IMDP_H */

@@ -1,0 +1,328 @@
+"""ctypes binding of include/imdp.h: the same entry points, argument marshalling only.
+
+Buffers may be numpy arrays (host) or CUDA torch tensors (device); pointers are
+passed through unchanged and every computation runs in the CUDA library.  The
+library is loaded from the package's ``_build`` directory; a missing library is
+an error (there is no CPU fallback)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+IMDP_OK, IMDP_EINVAL, IMDP_EINFEASIBLE, IMDP_ENOMEM, IMDP_EDEVICE = 0, 1, 2, 3, 4
+IMDP_ETIMEOUT, IMDP_EBUSY, IMDP_ENOCONV, IMDP_ENOTFOUND, IMDP_EPENDING = 5, 6, 7, 8, 9
+IMDP_F64, IMDP_F32 = 0, 1
+IMDP_REACH, IMDP_REACH_AVOID, IMDP_REWARD = 0, 1, 2
+
+STATUS_NAMES = {0: "ok", 1: "einval", 2: "einfeasible", 3: "enomem", 4: "edevice", 5: "etimeout", 6: "ebusy",
+                7: "enoconv", 8: "enotfound", 9: "epending"}
+
+# Every symbol include/imdp.h declares (checked by the tests).
+EXPORTED = [
+    "imdp_status_string", "imdp_last_error", "imdp_version", "imdp_create_csc", "imdp_create_dense",
+    "imdp_model_destroy", "imdp_model_info", "imdp_value_iteration", "imdp_value_iteration_batch",
+    "imdp_session_create", "imdp_session_reset", "imdp_session_step", "imdp_session_run", "imdp_session_read",
+    "imdp_session_launches", "imdp_session_destroy",
+]
+
+
+class ImdpError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} ({detail})")
+        self.status = status
+
+
+class imdp_spec(C.Structure):
+    _fields_ = [
+        ("property", C.c_int32),
+        ("infinite_time", C.c_int32),
+        ("horizon", C.c_int32),
+        ("eps", C.c_double),
+        ("pessimistic", C.c_int32),
+        ("maximize", C.c_int32),
+        ("reach", C.POINTER(C.c_int32)),
+        ("n_reach", C.c_int32),
+        ("avoid", C.POINTER(C.c_int32)),
+        ("n_avoid", C.c_int32),
+        ("reward", C.POINTER(C.c_double)),
+        ("discount", C.c_double),
+    ]
+
+
+_lib = None
+_LIB_PATH = _build.LIB
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load(path: Optional[str] = None):
+    """Load the CUDA library (it must have been built; see ``build.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"CUDA library not built: {p} (run python -m paper_2401_04068_gb300.build)")
+    lib = C.CDLL(p)
+    vp = C.c_void_p
+    lib.imdp_status_string.argtypes = [C.c_int]
+    lib.imdp_status_string.restype = C.c_char_p
+    lib.imdp_last_error.restype = C.c_char_p
+    lib.imdp_version.restype = C.c_char_p
+    lib.imdp_create_csc.argtypes = [C.c_int32, C.c_int32, C.c_int64, vp, vp, vp, vp, vp, C.c_int, vp,
+                                    C.POINTER(vp)]
+    lib.imdp_create_dense.argtypes = [C.c_int32, vp, vp, vp, C.c_int, vp, C.POINTER(vp)]
+    lib.imdp_model_destroy.argtypes = [vp]
+    lib.imdp_model_destroy.restype = None
+    lib.imdp_model_info.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_size_t), C.POINTER(C.c_int32)]
+    lib.imdp_value_iteration.argtypes = [vp, C.POINTER(imdp_spec), vp, C.POINTER(C.c_int32), vp, vp, vp]
+    lib.imdp_value_iteration_batch.argtypes = [C.POINTER(vp), C.POINTER(imdp_spec), C.c_int32, C.POINTER(vp),
+                                               C.POINTER(C.c_int32), vp]
+    lib.imdp_session_create.argtypes = [C.POINTER(vp), C.POINTER(imdp_spec), C.c_int32, vp, vp, C.POINTER(vp)]
+    lib.imdp_session_reset.argtypes = [vp, vp]
+    lib.imdp_session_step.argtypes = [vp, C.c_int32, vp]
+    lib.imdp_session_run.argtypes = [vp, C.c_int32, vp]
+    lib.imdp_session_read.argtypes = [vp, C.c_int32, vp, C.POINTER(C.c_int32), vp, vp, vp]
+    lib.imdp_session_launches.argtypes = [vp]
+    lib.imdp_session_launches.restype = C.c_int64
+    lib.imdp_session_destroy.argtypes = [vp]
+    lib.imdp_session_destroy.restype = None
+    for f in ("imdp_create_csc", "imdp_create_dense", "imdp_model_info", "imdp_value_iteration",
+              "imdp_value_iteration_batch", "imdp_session_create", "imdp_session_reset", "imdp_session_step",
+              "imdp_session_run", "imdp_session_read"):
+        getattr(lib, f).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(x) -> Optional[int]:
+    """Raw address of a numpy array or a torch tensor (None stays None)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffers must be contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("buffers must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def _check(status: int, where: str):
+    if status != IMDP_OK:
+        raise ImdpError(status, where, load().imdp_last_error().decode())
+
+
+def imdp_status_string(status: int) -> str:
+    return load().imdp_status_string(int(status)).decode()
+
+
+def imdp_last_error() -> str:
+    return load().imdp_last_error().decode()
+
+
+def imdp_version() -> str:
+    return load().imdp_version().decode()
+
+
+class Model:
+    """Owns an ``imdp_model*``; frees it on ``close()`` / garbage collection."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            load().imdp_model_destroy(C.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        ns, nc, nz, mc = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32()
+        by = C.c_size_t()
+        _check(load().imdp_model_info(C.c_void_p(self.handle), C.byref(ns), C.byref(nc), C.byref(nz), C.byref(by),
+                                      C.byref(mc)), "imdp_model_info")
+        return dict(n_states=ns.value, n_cols=nc.value, nnz=nz.value, device_bytes=by.value, max_col_nnz=mc.value)
+
+
+def imdp_create_csc(n_states, n_cols, nnz, stateptr, colptr, rowval, lower, upper, dtype=IMDP_F64,
+                    stream=None) -> Model:
+    out = C.c_void_p()
+    st = load().imdp_create_csc(int(n_states), int(n_cols), int(nnz), _ptr(stateptr), _ptr(colptr), _ptr(rowval),
+                                _ptr(lower), _ptr(upper), int(dtype), _stream(stream), C.byref(out))
+    _check(st, "imdp_create_csc")
+    return Model(out.value)
+
+
+def imdp_create_dense(n_states, n_actions, lower, upper, dtype=IMDP_F64, stream=None) -> Model:
+    out = C.c_void_p()
+    st = load().imdp_create_dense(int(n_states), _ptr(n_actions), _ptr(lower), _ptr(upper), int(dtype),
+                                  _stream(stream), C.byref(out))
+    _check(st, "imdp_create_dense")
+    return Model(out.value)
+
+
+def imdp_model_destroy(model: Model):
+    model.close()
+
+
+def make_spec(property=IMDP_REACH, infinite_time=False, horizon=100, eps=1e-6, pessimistic=True, maximize=True,
+              reach=(), avoid=(), reward=None, discount=1.0):
+    """Build an ``imdp_spec`` plus the arrays it points to (keep both alive)."""
+    keep = []
+    r = np.ascontiguousarray(reach, dtype=np.int32)
+    a = np.ascontiguousarray(avoid, dtype=np.int32)
+    keep += [r, a]
+    rw = None
+    if reward is not None:
+        rw = np.ascontiguousarray(reward, dtype=np.float64)
+        keep.append(rw)
+    s = imdp_spec(int(property), int(bool(infinite_time)), int(horizon), float(eps), int(bool(pessimistic)),
+                  int(bool(maximize)), r.ctypes.data_as(C.POINTER(C.c_int32)), int(r.size),
+                  a.ctypes.data_as(C.POINTER(C.c_int32)), int(a.size),
+                  rw.ctypes.data_as(C.POINTER(C.c_double)) if rw is not None else None, float(discount))
+    s._keep = keep
+    return s
+
+
+def imdp_value_iteration(model: Model, spec, V_out, k_out=None, residual_out=None, policy_out=None, stream=None,
+                         check=True) -> int:
+    """Raw call: V_out / residual_out / policy_out are caller buffers (host numpy
+    or device torch). Returns the status; k is written to ``k_out[0]`` when given."""
+    k = C.c_int32(0)
+    st = load().imdp_value_iteration(C.c_void_p(model.handle), C.byref(spec), _ptr(V_out), C.byref(k),
+                                     _ptr(residual_out), _ptr(policy_out), _stream(stream))
+    if k_out is not None:
+        k_out[0] = k.value
+    if check and st not in (IMDP_OK, IMDP_ENOCONV):
+        _check(st, "imdp_value_iteration")
+    return st
+
+
+def imdp_value_iteration_batch(models: Sequence[Model], specs: Sequence, V_out: Sequence, k_out=None, stream=None,
+                               check=True) -> int:
+    n = len(models)
+    hs = (C.c_void_p * n)(*[m.handle for m in models])
+    sp = (imdp_spec * n)(*specs)
+    vo = (C.c_void_p * n)(*[_ptr(v) for v in V_out])
+    ks = (C.c_int32 * n)()
+    st = load().imdp_value_iteration_batch(hs, sp, n, vo, ks, _stream(stream))
+    if k_out is not None:
+        for i in range(n):
+            k_out[i] = ks[i]
+    if check and st not in (IMDP_OK, IMDP_ENOCONV):
+        _check(st, "imdp_value_iteration_batch")
+    return st
+
+
+class Session:
+    """Owns an ``imdp_session*`` (resident value-iteration state for a batch)."""
+
+    def __init__(self, handle: int, models):
+        self.handle = handle
+        self._models = list(models)  # keep the models alive
+
+    def close(self):
+        if self.handle:
+            load().imdp_session_destroy(C.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def imdp_session_create(models: Sequence[Model], specs: Sequence, want_policy=None, stream=None) -> Session:
+    n = len(models)
+    hs = (C.c_void_p * n)(*[m.handle for m in models])
+    sp = (imdp_spec * n)(*specs)
+    wp = None
+    if want_policy is not None:
+        wp = np.ascontiguousarray(want_policy, dtype=np.int32)
+    out = C.c_void_p()
+    st = load().imdp_session_create(hs, sp, n, _ptr(wp), _stream(stream), C.byref(out))
+    _check(st, "imdp_session_create")
+    return Session(out.value, models)
+
+
+def imdp_session_reset(s: Session, stream=None):
+    _check(load().imdp_session_reset(C.c_void_p(s.handle), _stream(stream)), "imdp_session_reset")
+
+
+def imdp_session_step(s: Session, n_iters: int, stream=None):
+    _check(load().imdp_session_step(C.c_void_p(s.handle), int(n_iters), _stream(stream)), "imdp_session_step")
+
+
+def imdp_session_run(s: Session, check_every: int = 32, stream=None):
+    _check(load().imdp_session_run(C.c_void_p(s.handle), int(check_every), _stream(stream)), "imdp_session_run")
+
+
+def imdp_session_read(s: Session, index: int, V_out=None, k_out=None, residual_out=None, policy_out=None,
+                      stream=None, check=True) -> int:
+    k = C.c_int32(0)
+    st = load().imdp_session_read(C.c_void_p(s.handle), int(index), _ptr(V_out), C.byref(k), _ptr(residual_out),
+                                  _ptr(policy_out), _stream(stream))
+    if k_out is not None:
+        k_out[0] = k.value
+    if check and st not in (IMDP_OK, IMDP_ENOCONV):
+        _check(st, "imdp_session_read")
+    return st
+
+
+def imdp_session_launches(s: Session) -> int:
+    return int(load().imdp_session_launches(C.c_void_p(s.handle)))
+
+
+def imdp_session_destroy(s: Session):
+    s.close()
+
+
+# ---------------------------------------------------------------- convenience wrappers (host numpy in/out)
+
+def create_model(m, dtype=IMDP_F64, stream=None) -> Model:
+    """Model from any object with n_states/stateptr/colptr/rowval/lower/upper."""
+    return imdp_create_csc(m.n_states, len(m.colptr) - 1, len(m.rowval), np.ascontiguousarray(m.stateptr, np.int32),
+                           np.ascontiguousarray(m.colptr, np.int32), np.ascontiguousarray(m.rowval, np.int32),
+                           np.ascontiguousarray(m.lower, np.float64), np.ascontiguousarray(m.upper, np.float64),
+                           dtype, stream)
+
+
+def value_iteration(model: Model, n_states: int, policy: bool = False, stream=None, **spec_kw):
+    """Returns (status, V, k, residual, policy_or_None) as host numpy arrays."""
+    spec = make_spec(**spec_kw)
+    V = np.zeros(n_states, np.float64)
+    res = np.zeros(n_states, np.float64)
+    pol = None
+    if policy:
+        rows = 1 if spec_kw.get("infinite_time") else int(spec_kw.get("horizon", 100))
+        pol = np.zeros((rows, n_states), np.int32)
+    k = [0]
+    st = imdp_value_iteration(model, spec, V, k, res, pol, stream)
+    return STATUS_NAMES[st], V, k[0], res, pol

@@ -1,0 +1,159 @@
+// Internal declarations shared by the library's translation units.
+//
+// Number format. Every probability bound and every value-function entry of a
+// reachability problem lies in [0, 1] (Sec. 2). The kernels keep them as
+// unsigned 64-bit fixed point with 63 fractional bits ("Q1.63": x -> round(x * 2^63),
+// 1.0 = 2^63). Bellman arithmetic is then integer: products use the high half of a
+// 64x64-bit multiply, sums are exact and associative, so results do not depend on
+// the reduction order or on the thread mapping. On GB300 the FP64 pipe issues ~60x
+// fewer operations per cycle than the 32-bit integer/FP32 pipes, which is why the
+// hot loop avoids binary64 altogether.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/imdp.h"
+
+namespace imdp {
+
+constexpr uint64_t kOne = 1ull << 63;  // 1.0 in Q1.63
+
+// Column-size classes of the register-resident column routine: a warp keeps
+// up to 32 * E entries of one column in registers.
+constexpr int kWarpsPerBlock = 8;
+constexpr int kThreads = 32 * kWarpsPerBlock;
+
+// Property kinds inside the kernels.
+enum : int32_t { kPropReach = 0, kPropReachAvoid = 1, kPropReward = 2 };
+
+// Device-resident model (the "IntervalMDP.cu(problem)" transfer of Sec. 3.2,
+// CSC layout of Sec. 3.1 / Appendix A).
+struct DevModel {
+  int32_t n_states = 0;
+  int32_t n_cols = 0;
+  int64_t nnz = 0;
+  int32_t max_col = 0;     // largest column (entries)
+  int32_t dtype = IMDP_F64;
+  int32_t* stateptr = nullptr;  // n_states + 1
+  int32_t* colptr = nullptr;    // n_cols + 1
+  int32_t* rowval = nullptr;    // nnz
+  ulonglong2* lg = nullptr;     // nnz x {lower, gap = upper - lower} in Q1.63
+  uint64_t* rem = nullptr;      // n_cols: 1 - sum(lower) in Q1.63 (clamped at 0)
+  size_t bytes = 0;
+};
+
+// One problem of a batch as the step kernel sees it (read-only during a launch).
+struct Problem {
+  const int32_t* stateptr;
+  const int32_t* colptr;
+  const int32_t* rowval;
+  const ulonglong2* lg;
+  const uint64_t* rem;
+  const uint8_t* fixed;   // n_states: 0 free, 1 held at 1 (reach target), 2 held at 0 (avoid)
+  uint64_t* V[2];         // ping-pong value buffers; iteration k writes V[k & 1]
+  int32_t* policy;        // nullable; see policy_mode
+  const uint64_t* rbias;  // reward: per-state additive term (normalised), nullable
+  int32_t n_states;
+  int32_t pessimistic;
+  int32_t maximize;
+  int32_t property;
+  int32_t horizon;        // K (finite) or iteration cap (infinite)
+  int32_t infinite;
+  int32_t policy_mode;    // 0 none, 1 time-dependent K x n, 2 stationary n
+  int32_t _pad;
+  uint64_t eps_fix;       // infinite horizon: stop when max |dV| < eps_fix
+  uint64_t gamma_fix;     // reward: discount in Q1.63
+};
+
+// Mutable per-problem iteration state (device memory).
+struct IterState {
+  int32_t iter;     // completed iterations
+  int32_t done;     // 1 once the problem has finished
+  int32_t k_final;  // iterations performed when done
+  int32_t noconv;   // infinite horizon stopped at the cap
+  unsigned long long resmax;  // max |V_k - V_{k-1}| of the running iteration
+};
+
+struct StepControl {
+  unsigned int finished;  // blocks finished in the running launch
+  unsigned int pad;
+};
+
+struct StepLaunch {
+  const Problem* probs;
+  IterState* its;
+  const int32_t* state_base;  // count + 1 prefix of n_states
+  StepControl* ctl;
+  int32_t count;
+  int32_t total_states;
+  int32_t any_infinite;
+  int32_t col_class;  // register class E of the column routine
+};
+
+// bellman.cu
+cudaError_t launch_bellman_step(const StepLaunch& L, int grid, cudaStream_t st);
+int choose_col_class(int32_t max_col);
+int bellman_grid(int total_states, int col_class);
+
+// model.cu
+imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, const int32_t* stateptr,
+                             const int32_t* colptr, const int32_t* rowval, const double* lower,
+                             const double* upper, imdp_dtype dtype, cudaStream_t st, DevModel** out);
+void model_destroy(DevModel* m);
+
+// session.cu: resident device state of value iteration for a batch of problems.
+struct Session {
+  int device = 0;
+  int count = 0;
+  int64_t total = 0;
+  std::vector<DevModel*> models;
+  std::vector<Problem> probs_h;
+  std::vector<int32_t> base_h;
+  std::vector<int64_t> policy_cells;
+  int32_t max_horizon = 0;
+  bool any_infinite = false;
+  uint8_t* fixed = nullptr;
+  uint64_t* V = nullptr;
+  int32_t* base = nullptr;
+  Problem* probs = nullptr;
+  IterState* its = nullptr;
+  StepControl* ctl = nullptr;
+  StepLaunch L{};
+  int grid = 1;
+  cudaGraphExec_t graph = nullptr;
+  int64_t launches = 0;
+  int64_t launched_since_reset = 0;
+  std::vector<void*> allocs;
+
+  ~Session();
+  template <class T> T* alloc(size_t n);
+  static imdp_status create(const std::vector<DevModel*>& ms, const std::vector<const imdp_spec*>& specs,
+                            const int32_t* want_policy, cudaStream_t st, Session** out);
+  imdp_status reset(cudaStream_t st);
+  imdp_status step(int32_t n, cudaStream_t st);
+  imdp_status run(int32_t check_every, cudaStream_t st);
+  imdp_status read_states(std::vector<IterState>& out, cudaStream_t st);
+  imdp_status read(int32_t p, double* V_out, int32_t* k_out, double* res_out, int32_t* pol_out, cudaStream_t st);
+};
+imdp_status check_spec(const DevModel* m, const imdp_spec* sp);
+
+// api.cu
+void set_error(const std::string& msg);
+bool is_device_pointer(const void* p);
+imdp_status cuda_status(cudaError_t e, const char* where);
+
+}  // namespace imdp
+
+struct imdp_model {
+  imdp::DevModel* dev;
+  int device;
+};
+
+struct imdp_session {
+  imdp::Session* s;
+};

@@ -1,0 +1,195 @@
+// Model creation: copy CSC arrays to the device, check feasibility of every
+// column (Sec. 2: 0 <= P_lo <= P_up <= 1 and sum P_lo <= 1 <= sum P_up) and
+// convert the bounds to the kernels' Q1.63 fixed point as (lower, gap) pairs
+// plus rem = 1 - sum(lower) per column (the quantities of the O-maximization
+// procedure, Sec. 4; the paper also stores lower and gap, Sec. 5).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "imdp_internal.h"
+
+namespace imdp {
+
+namespace {
+
+constexpr double kFeasTol = 1e-12;
+enum : unsigned { kErrStruct = 1u, kErrInfeasible = 2u };
+
+// One warp per column: range/order checks of the destinations, bound checks,
+// binary64 sums for the feasibility test, and the fixed-point conversion.
+__global__ void convert_columns_kernel(int32_t n_states, int32_t n_cols, const int32_t* __restrict__ colptr,
+                                       const int32_t* __restrict__ rowval, const double* __restrict__ lower,
+                                       const double* __restrict__ upper, ulonglong2* __restrict__ lg,
+                                       uint64_t* __restrict__ rem, unsigned* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (int32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n_cols; j += warps) {
+    const int32_t a = colptr[j], b = colptr[j + 1];
+    double slo = 0.0, sup = 0.0;
+    unsigned long long lsum = 0;
+    unsigned bad = 0;
+    for (int32_t i = a + lane; i < b; i += 32) {
+      const int32_t r = rowval[i];
+      if (r < 0 || r >= n_states) bad |= kErrStruct;
+      if (i > a && rowval[i - 1] >= r) bad |= kErrStruct;
+      const double lo = lower[i], up = upper[i];
+      if (!(lo >= 0.0) || !(up <= 1.0) || !(lo <= up)) {
+        bad |= kErrInfeasible;
+        lg[i] = make_ulonglong2(0, 0);
+        continue;
+      }
+      slo += lo;
+      sup += up;
+      const unsigned long long L = __double2ull_rn(lo * 9223372036854775808.0);
+      const unsigned long long U = __double2ull_rn(up * 9223372036854775808.0);
+      lg[i] = make_ulonglong2(L, U - L);
+      const unsigned long long t = lsum + L;
+      if (t < lsum) bad |= kErrInfeasible;  // sum of lower bounds far above 1
+      lsum = t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      slo += __shfl_xor_sync(0xffffffffu, slo, o);
+      sup += __shfl_xor_sync(0xffffffffu, sup, o);
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, lsum, o);
+      if (lsum + t < lsum) bad |= kErrInfeasible;
+      lsum += t;
+      bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if (lane == 0) {
+      if (slo > 1.0 + kFeasTol || sup < 1.0 - kFeasTol) bad |= kErrInfeasible;
+      rem[j] = lsum >= kOne ? 0ull : kOne - lsum;
+      if (bad) atomicOr(err, bad);
+    }
+  }
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+}  // namespace
+
+void model_destroy(DevModel* m) {
+  if (!m) return;
+  cudaFree(m->stateptr);
+  cudaFree(m->colptr);
+  cudaFree(m->rowval);
+  cudaFree(m->lg);
+  cudaFree(m->rem);
+  delete m;
+}
+
+imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, const int32_t* stateptr,
+                             const int32_t* colptr, const int32_t* rowval, const double* lower,
+                             const double* upper, imdp_dtype dtype, cudaStream_t st, DevModel** out) {
+  if (!out) { set_error("out is NULL"); return IMDP_EINVAL; }
+  *out = nullptr;
+  if (n_states < 1 || n_cols < n_states || nnz < 0 || nnz >= (int64_t(1) << 31)) {
+    set_error("dimensions out of range (need n_states >= 1, n_cols >= n_states, 0 <= nnz < 2^31)");
+    return IMDP_EINVAL;
+  }
+  if (!stateptr || !colptr || (nnz > 0 && (!rowval || !lower || !upper))) {
+    set_error("NULL array");
+    return IMDP_EINVAL;
+  }
+  if (dtype != IMDP_F64) {
+    set_error("only IMDP_F64 storage is supported by this build");
+    return IMDP_EINVAL;
+  }
+  // Structure arrays are small (states + columns): check them on the host.
+  std::vector<int32_t> hs(n_states + 1), hc(n_cols + 1);
+  cudaError_t e;
+  e = cudaMemcpyAsync(hs.data(), stateptr, sizeof(int32_t) * hs.size(), cudaMemcpyDefault, st);
+  if (e != cudaSuccess) return cuda_status(e, "copy stateptr");
+  e = cudaMemcpyAsync(hc.data(), colptr, sizeof(int32_t) * hc.size(), cudaMemcpyDefault, st);
+  if (e != cudaSuccess) return cuda_status(e, "copy colptr");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "sync");
+  if (hs[0] != 0 || hs[n_states] != n_cols) { set_error("stateptr must start at 0 and end at n_cols"); return IMDP_EINVAL; }
+  for (int32_t s = 0; s < n_states; ++s)
+    if (hs[s + 1] <= hs[s]) { set_error("every state needs at least one action (stateptr strictly increasing)"); return IMDP_EINVAL; }
+  if (hc[0] != 0 || hc[n_cols] != nnz) { set_error("colptr must start at 0 and end at nnz"); return IMDP_EINVAL; }
+  int32_t max_col = 0;
+  for (int32_t j = 0; j < n_cols; ++j) {
+    const int32_t k = hc[j + 1] - hc[j];
+    if (k < 0) { set_error("colptr must be nondecreasing"); return IMDP_EINVAL; }
+    max_col = std::max(max_col, k);
+  }
+
+  DevModel* m = new DevModel();
+  m->n_states = n_states;
+  m->n_cols = n_cols;
+  m->nnz = nnz;
+  m->max_col = max_col;
+  m->dtype = dtype;
+  const size_t nz = (size_t)std::max<int64_t>(nnz, 1);
+  const bool ok = cudaMalloc(&m->stateptr, sizeof(int32_t) * (n_states + 1)) == cudaSuccess &&
+                  cudaMalloc(&m->colptr, sizeof(int32_t) * (n_cols + 1)) == cudaSuccess &&
+                  cudaMalloc(&m->rowval, sizeof(int32_t) * nz) == cudaSuccess &&
+                  cudaMalloc(&m->lg, sizeof(ulonglong2) * nz) == cudaSuccess &&
+                  cudaMalloc(&m->rem, sizeof(uint64_t) * n_cols) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    model_destroy(m);
+    set_error("device allocation failed for the model");
+    return IMDP_ENOMEM;
+  }
+  m->bytes = sizeof(int32_t) * (n_states + 1 + n_cols + 1 + nz) + sizeof(ulonglong2) * nz + sizeof(uint64_t) * n_cols;
+
+  // Bounds: device pointers are used in place, host arrays are staged.
+  DevBuf dlo, dup, derr;
+  const double* lo_d = lower;
+  const double* up_d = upper;
+  if (nnz > 0 && !is_device_pointer(lower)) {
+    if (cudaMalloc(&dlo.p, sizeof(double) * nz) != cudaSuccess) { cudaGetLastError(); model_destroy(m); set_error("staging allocation failed"); return IMDP_ENOMEM; }
+    lo_d = (const double*)dlo.p;
+  }
+  if (nnz > 0 && !is_device_pointer(upper)) {
+    if (cudaMalloc(&dup.p, sizeof(double) * nz) != cudaSuccess) { cudaGetLastError(); model_destroy(m); set_error("staging allocation failed"); return IMDP_ENOMEM; }
+    up_d = (const double*)dup.p;
+  }
+  if (cudaMalloc(&derr.p, sizeof(unsigned)) != cudaSuccess) { cudaGetLastError(); model_destroy(m); set_error("allocation failed"); return IMDP_ENOMEM; }
+
+  e = cudaMemcpyAsync(m->stateptr, hs.data(), sizeof(int32_t) * hs.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->colptr, hc.data(), sizeof(int32_t) * hc.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(m->rowval, rowval, sizeof(int32_t) * nnz, cudaMemcpyDefault, st);
+  if (e == cudaSuccess && lo_d != lower) e = cudaMemcpyAsync((void*)lo_d, lower, sizeof(double) * nnz, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && up_d != upper) e = cudaMemcpyAsync((void*)up_d, upper, sizeof(double) * nnz, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(derr.p, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) { model_destroy(m); return cuda_status(e, "upload model"); }
+
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int warps_needed = n_cols;
+  int grid = std::min((warps_needed + 7) / 8, sms * 16);
+  if (grid < 1) grid = 1;
+  convert_columns_kernel<<<grid, 256, 0, st>>>(n_states, n_cols, m->colptr, m->rowval, lo_d, up_d, m->lg, m->rem,
+                                               (unsigned*)derr.p);
+  e = cudaGetLastError();
+  unsigned herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { model_destroy(m); return cuda_status(e, "convert model"); }
+  if (herr & kErrStruct) {
+    model_destroy(m);
+    set_error("rowval out of range or not strictly increasing within a column");
+    return IMDP_EINVAL;
+  }
+  if (herr & kErrInfeasible) {
+    model_destroy(m);
+    set_error("infeasible column: need 0 <= lower <= upper <= 1 and sum lower <= 1 <= sum upper (tol 1e-12)");
+    return IMDP_EINFEASIBLE;
+  }
+  *out = m;
+  return IMDP_OK;
+}
+
+}  // namespace imdp

@@ -1,0 +1,309 @@
+// Resident solver sessions: device state of value iteration (Eq. 2) for a batch
+// of problems, the iteration driver (graph-captured chunks of Bellman steps)
+// and the export of (V, k, residual, policy) as value_iteration returns them
+// (Sec. 3.2).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "imdp_internal.h"
+
+namespace imdp {
+
+namespace {
+
+__global__ void init_values_kernel(int64_t n, const uint8_t* __restrict__ fixed, uint64_t* __restrict__ V0) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    V0[i] = fixed[i] == 1 ? kOne : 0ull;
+}
+
+// V (Q1.63) -> binary64; with `prev`, writes V - prev (the Bellman residual).
+__global__ void export_values_kernel(int32_t n, const uint64_t* __restrict__ V, const uint64_t* __restrict__ prev,
+                                     double* __restrict__ out) {
+  const double scale = 1.0 / 9223372036854775808.0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (prev) {
+      const uint64_t a = V[i], b = prev[i];
+      out[i] = a >= b ? (double)(a - b) * scale : -(double)(b - a) * scale;
+    } else {
+      out[i] = (double)V[i] * scale;
+    }
+  }
+}
+
+__global__ void fill_i32_kernel(int64_t n, int32_t* p, int32_t v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// eps in Q1.63 rounded up, so an integer residual r satisfies r < eps_fix
+// exactly when r * 2^-63 < eps.
+uint64_t eps_to_fixed(double eps) {
+  if (eps >= 1.0) return kOne + 1;
+  const double x = eps * 9223372036854775808.0;
+  uint64_t f = (uint64_t)x;
+  if ((double)f < x) f += 1;
+  return f;
+}
+
+constexpr int kGraphChunk = 16;
+
+}  // namespace
+
+imdp_status check_spec(const DevModel* m, const imdp_spec* sp) {
+  if (!sp) { set_error("spec is NULL"); return IMDP_EINVAL; }
+  if (sp->property != IMDP_REACH && sp->property != IMDP_REACH_AVOID && sp->property != IMDP_REWARD) {
+    set_error("unknown property"); return IMDP_EINVAL;
+  }
+  if (sp->property == IMDP_REWARD) {
+    set_error("reward properties are not supported by this build"); return IMDP_EINVAL;
+  }
+  if (sp->horizon < 0) { set_error("horizon must be >= 0"); return IMDP_EINVAL; }
+  if (sp->infinite_time && !(sp->eps > 0.0)) { set_error("eps must be > 0 for an infinite horizon"); return IMDP_EINVAL; }
+  if (sp->n_reach < 0 || (sp->n_reach > 0 && !sp->reach)) { set_error("bad reach set"); return IMDP_EINVAL; }
+  if (sp->property == IMDP_REACH_AVOID && (sp->n_avoid < 0 || (sp->n_avoid > 0 && !sp->avoid))) {
+    set_error("bad avoid set"); return IMDP_EINVAL;
+  }
+  for (int32_t i = 0; i < sp->n_reach; ++i)
+    if (sp->reach[i] < 0 || sp->reach[i] >= m->n_states) { set_error("reach state out of range"); return IMDP_EINVAL; }
+  if (sp->property == IMDP_REACH_AVOID)
+    for (int32_t i = 0; i < sp->n_avoid; ++i)
+      if (sp->avoid[i] < 0 || sp->avoid[i] >= m->n_states) { set_error("avoid state out of range"); return IMDP_EINVAL; }
+  return IMDP_OK;
+}
+
+Session::~Session() {
+  if (graph) cudaGraphExecDestroy(graph);
+  for (void* p : allocs) cudaFree(p);
+}
+
+template <class T>
+T* Session::alloc(size_t n) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  allocs.push_back(p);
+  return (T*)p;
+}
+
+imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<const imdp_spec*>& specs,
+                            const int32_t* want_policy, cudaStream_t st, Session** out) {
+  *out = nullptr;
+  const int count = (int)ms.size();
+  for (int p = 0; p < count; ++p) {
+    imdp_status s = check_spec(ms[p], specs[p]);
+    if (s != IMDP_OK) return s;
+  }
+  Session* S = new Session();
+  S->count = count;
+  S->models = ms;
+  cudaGetDevice(&S->device);
+  S->base_h.assign(count + 1, 0);
+  for (int p = 0; p < count; ++p) S->base_h[p + 1] = S->base_h[p] + ms[p]->n_states;
+  const int64_t total = S->base_h[count];
+  if (total >= (int64_t(1) << 31)) { delete S; set_error("batch too large"); return IMDP_EINVAL; }
+  S->total = total;
+  std::vector<uint8_t> fixed((size_t)total, 0);
+  int max_class = 1;
+  for (int p = 0; p < count; ++p) {
+    const imdp_spec* sp = specs[p];
+    uint8_t* f = fixed.data() + S->base_h[p];
+    for (int32_t i = 0; i < sp->n_reach; ++i) f[sp->reach[i]] = 1;
+    if (sp->property == IMDP_REACH_AVOID)
+      for (int32_t i = 0; i < sp->n_avoid; ++i) {
+        if (f[sp->avoid[i]] == 1) { delete S; set_error("a state is in both the reach and the avoid set"); return IMDP_EINVAL; }
+        f[sp->avoid[i]] = 2;
+      }
+    max_class = std::max(max_class, choose_col_class(ms[p]->max_col));
+  }
+  S->fixed = S->alloc<uint8_t>(total);
+  S->V = S->alloc<uint64_t>(2 * total);
+  S->base = S->alloc<int32_t>(count + 1);
+  S->probs = S->alloc<Problem>(count);
+  S->its = S->alloc<IterState>(count);
+  S->ctl = S->alloc<StepControl>(1);
+  if (!S->fixed || !S->V || !S->base || !S->probs || !S->its || !S->ctl) {
+    delete S; set_error("device allocation failed (session)"); return IMDP_ENOMEM;
+  }
+  S->probs_h.resize(count);
+  S->policy_cells.assign(count, 0);
+  for (int p = 0; p < count; ++p) {
+    DevModel* m = ms[p];
+    const imdp_spec* sp = specs[p];
+    Problem& P = S->probs_h[p];
+    std::memset(&P, 0, sizeof(P));
+    P.stateptr = m->stateptr;
+    P.colptr = m->colptr;
+    P.rowval = m->rowval;
+    P.lg = m->lg;
+    P.rem = m->rem;
+    P.fixed = S->fixed + S->base_h[p];
+    P.V[0] = S->V + S->base_h[p];
+    P.V[1] = S->V + total + S->base_h[p];
+    P.n_states = m->n_states;
+    P.pessimistic = sp->pessimistic ? 1 : 0;
+    P.maximize = sp->maximize ? 1 : 0;
+    P.property = sp->property;
+    P.infinite = sp->infinite_time ? 1 : 0;
+    P.horizon = sp->infinite_time ? (sp->horizon > 0 ? sp->horizon : 1000000) : sp->horizon;
+    P.eps_fix = sp->infinite_time ? eps_to_fixed(sp->eps) : 0;
+    S->max_horizon = std::max(S->max_horizon, P.horizon);
+    S->any_infinite = S->any_infinite || P.infinite;
+    if (want_policy && want_policy[p]) {
+      const size_t cells = (size_t)(P.infinite ? 1 : P.horizon) * m->n_states;
+      P.policy = S->alloc<int32_t>(cells);
+      if (!P.policy) { delete S; set_error("device allocation failed (policy)"); return IMDP_ENOMEM; }
+      P.policy_mode = P.infinite ? 2 : 1;
+      S->policy_cells[p] = (int64_t)cells;
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(S->fixed, fixed.data(), total, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->base, S->base_h.data(), sizeof(int32_t) * (count + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->probs, S->probs_h.data(), sizeof(Problem) * count, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host staging vectors go out of scope
+  if (e != cudaSuccess) { delete S; return cuda_status(e, "session setup"); }
+  S->L.probs = S->probs;
+  S->L.its = S->its;
+  S->L.state_base = S->base;
+  S->L.ctl = S->ctl;
+  S->L.count = count;
+  S->L.total_states = (int32_t)total;
+  S->L.any_infinite = S->any_infinite ? 1 : 0;
+  S->L.col_class = max_class;
+  S->grid = bellman_grid((int)total, max_class);
+  imdp_status r = S->reset(st);
+  if (r != IMDP_OK) { delete S; return r; }
+  *out = S;
+  return IMDP_OK;
+}
+
+imdp_status Session::reset(cudaStream_t st) {
+  init_values_kernel<<<(int)std::min<int64_t>((total + 255) / 256, 8192), 256, 0, st>>>(total, fixed, V);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemsetAsync(its, 0, sizeof(IterState) * count, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(StepControl), st);
+  for (int p = 0; p < count && e == cudaSuccess; ++p)
+    if (policy_cells[p] > 0) {
+      fill_i32_kernel<<<(int)std::min<int64_t>((policy_cells[p] + 255) / 256, 4096), 256, 0, st>>>(
+          policy_cells[p], probs_h[p].policy, -1);
+      e = cudaGetLastError();
+    }
+  if (e != cudaSuccess) return cuda_status(e, "session reset");
+  launched_since_reset = 0;
+  return IMDP_OK;
+}
+
+imdp_status Session::step(int32_t n, cudaStream_t st) {
+  if (n <= 0) return IMDP_OK;
+  cudaError_t e = cudaSuccess;
+  int32_t done = 0;
+  if (st != nullptr && n >= kGraphChunk) {
+    if (!graph) {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      for (int i = 0; i < kGraphChunk && e == cudaSuccess; ++i) e = launch_bellman_step(L, grid, st);
+      cudaError_t e2 = cudaStreamEndCapture(st, &g);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        graph = nullptr;
+        return cuda_status(e, "graph capture");
+      }
+    }
+    for (; done + kGraphChunk <= n && e == cudaSuccess; done += kGraphChunk) e = cudaGraphLaunch(graph, st);
+  }
+  for (; done < n && e == cudaSuccess; ++done) e = launch_bellman_step(L, grid, st);
+  if (e != cudaSuccess) return cuda_status(e, "bellman step");
+  launches += n;
+  launched_since_reset += n;
+  return IMDP_OK;
+}
+
+imdp_status Session::read_states(std::vector<IterState>& out, cudaStream_t st) {
+  out.resize(count);
+  cudaError_t e = cudaMemcpyAsync(out.data(), its, sizeof(IterState) * count, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "read iteration state");
+  return IMDP_OK;
+}
+
+imdp_status Session::run(int32_t check_every, cudaStream_t st) {
+  if (!any_infinite) {
+    // Every problem finishes within max_horizon launches of the reset.
+    return step(std::max<int32_t>(0, max_horizon - (int32_t)std::min<int64_t>(launched_since_reset, max_horizon)), st);
+  }
+  if (check_every <= 0) check_every = 32;
+  std::vector<IterState> s;
+  while (launched_since_reset < max_horizon) {
+    const int32_t n = (int32_t)std::min<int64_t>(check_every, max_horizon - launched_since_reset);
+    imdp_status r = step(n, st);
+    if (r != IMDP_OK) return r;
+    r = read_states(s, st);
+    if (r != IMDP_OK) return r;
+    bool all = true;
+    for (int p = 0; p < count; ++p) all = all && s[p].done;
+    if (all) break;
+  }
+  return IMDP_OK;
+}
+
+imdp_status Session::read(int32_t p, double* V_out, int32_t* k_out, double* res_out, int32_t* pol_out,
+                          cudaStream_t st) {
+  if (p < 0 || p >= count) { set_error("problem index out of range"); return IMDP_EINVAL; }
+  std::vector<IterState> s;
+  imdp_status r = read_states(s, st);
+  if (r != IMDP_OK) return r;
+  const Problem& P = probs_h[p];
+  const int32_t k = s[p].done ? s[p].k_final : s[p].iter;
+  if (k_out) *k_out = k;
+  const int32_t n = P.n_states;
+  const uint64_t* Vk = P.V[k & 1];
+  const uint64_t* Vk1 = P.V[(k + 1) & 1];
+  const int g = std::min((n + 255) / 256, 4096);
+  std::vector<void*> tmp;
+  auto cleanup = [&]() { for (void* t : tmp) cudaFree(t); };
+  auto emit = [&](double* out, const uint64_t* prev) -> cudaError_t {
+    if (!out) return cudaSuccess;
+    double* dst = out;
+    const bool host = !is_device_pointer(out);
+    if (host) {
+      void* t = nullptr;
+      cudaError_t ea = cudaMalloc(&t, sizeof(double) * std::max(n, 1));
+      if (ea != cudaSuccess) return ea;
+      tmp.push_back(t);
+      dst = (double*)t;
+    }
+    if (prev == nullptr || k >= 1) {
+      export_values_kernel<<<g, 256, 0, st>>>(n, Vk, prev, dst);
+    } else {
+      cudaMemsetAsync(dst, 0, sizeof(double) * n, st);
+    }
+    cudaError_t e2 = cudaGetLastError();
+    if (e2 == cudaSuccess && host) e2 = cudaMemcpyAsync(out, dst, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+    return e2;
+  };
+  cudaError_t e = emit(V_out, nullptr);
+  if (e == cudaSuccess) e = emit(res_out, Vk1);
+  if (e == cudaSuccess && pol_out) {
+    if (!P.policy) {
+      cleanup();
+      set_error("policy was not requested when the session was created");
+      return IMDP_EINVAL;
+    }
+    e = cudaMemcpyAsync(pol_out, P.policy, sizeof(int32_t) * policy_cells[p], cudaMemcpyDefault, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) return cuda_status(e, "session read");
+  if (s[p].noconv) {
+    set_error("infinite horizon did not converge within the iteration cap");
+    return IMDP_ENOCONV;
+  }
+  return IMDP_OK;
+}
+
+}  // namespace imdp

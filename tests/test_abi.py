@@ -1,0 +1,66 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+include/imdp.h declares. No compute call runs here (no GPU needed)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2401_04068_gb300 as pkg
+from paper_2401_04068_gb300 import build as pbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(imdp_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    return pbuild.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for must in ("imdp_create_csc", "imdp_value_iteration", "imdp_value_iteration_batch", "imdp_model_destroy"):
+        assert must in names
+    assert sorted(pkg.EXPORTED) == sorted(names)
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\s[TW]\s+(\S+)", out))
+    missing = [n for n in _declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_is_built_for_sm_103a(lib_path):
+    assert "arch=compute_103a,code=sm_103a" in " ".join(pbuild.ARCH)
+    assert os.path.getsize(lib_path) > 0
+
+
+def test_loads_and_reports_status_strings(lib_path):
+    lib = pkg.load()
+    assert pkg.imdp_status_string(0) == "ok"
+    assert pkg.imdp_status_string(2) == "infeasible interval model"
+    assert pkg.imdp_version().count(".") == 2
+    assert lib is pkg.load()
+
+
+def test_product_path_has_no_oracle_dependency():
+    # the package and its sources never import or link the oracle
+    for dirpath, _, files in os.walk(os.path.join(ROOT, "paper_2401_04068_gb300")):
+        if "_build" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".h", ".cuh")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text and "imdp_oracle" not in text, f

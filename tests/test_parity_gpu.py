@@ -1,0 +1,237 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2401_04068_gb300 as g
+from gpu_helpers import TOL_F64, check_policy_row, om, q_values, run_oracle
+from workloads import banded_batch, banded_imdp, concat_block_diagonal, make_config, random_imdp
+
+pytestmark = pytest.mark.gpu
+
+MODES = [(True, True), (True, False), (False, True), (False, False)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    g.load()
+
+
+def _model(m):
+    return g.create_model(m)
+
+
+def _compare(m, model, tol=TOL_F64, policy=False, **kw):
+    st, V, k, res, pol = g.value_iteration(model, m.n_states, policy=policy, **kw)
+    ost, oV, ok, ores, opol = run_oracle(m, policy=policy, **kw)
+    assert st == ost, (st, ost)
+    assert k == ok
+    np.testing.assert_allclose(V, oV, rtol=0, atol=tol)
+    np.testing.assert_allclose(res, ores, rtol=0, atol=tol)
+    return V, k, res, pol, oV
+
+
+# --------------------------------------------------------------------------- the paper's worked example
+
+@pytest.mark.parametrize("pess,maxi", MODES)
+def test_worked_example(worked_example, pess, maxi):
+    ex = worked_example
+    class M: pass
+    m = M()
+    for key in ("n_states", "stateptr", "colptr", "rowval", "lower", "upper"):
+        setattr(m, key, ex[key])
+    m.n_cols = len(ex["colptr"]) - 1
+    model = _model(m)
+    for K in (0, 1, 2, 7, ex["horizon"]):
+        _compare(m, model, horizon=K, reach=ex["goal"], pessimistic=pess, maximize=maxi)
+    st, V, k, res, pol = g.value_iteration(model, 3, policy=True, horizon=1, reach=ex["goal"])
+    np.testing.assert_allclose(V, [0.2, 0.4, 1.0], atol=1e-15)
+    assert list(pol[0]) == [0, 1, -1]
+
+
+# --------------------------------------------------------------------------- small random models, all modes
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("pess,maxi", MODES)
+def test_random_models(seed, pess, maxi):
+    m = random_imdp(40, max_actions=3, density=0.3 + 0.05 * seed, seed=seed)
+    model = _model(m)
+    V, k, res, pol, _ = _compare(m, model, policy=True, horizon=12, reach=m.goal, pessimistic=pess, maximize=maxi)
+    # policy at time 0 is the argmax of the last iteration: check it by Q-values
+    Vprev = V - res
+    check_policy_row(m, Vprev, pol[0], set(m.goal.tolist()), pess, maxi)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_ties_and_exact_grids(seed):
+    # bounds on a dyadic grid and many equal values: threshold ties everywhere
+    m = random_imdp(30, max_actions=2, density=0.5, seed=50 + seed, exact_grid=16)
+    model = _model(m)
+    for pess, maxi in MODES:
+        _compare(m, model, horizon=9, reach=m.goal, pessimistic=pess, maximize=maxi)
+
+
+def test_lower_equals_upper_and_rem_zero():
+    m = random_imdp(50, max_actions=2, density=0.2, seed=3, lower_equals_upper=True)
+    model = _model(m)
+    for pess, maxi in MODES:
+        _compare(m, model, horizon=20, reach=m.goal, pessimistic=pess, maximize=maxi)
+
+
+# --------------------------------------------------------------------------- column-size classes and ragged tails
+
+@pytest.mark.parametrize("k_mean", [3, 20, 45, 100, 200, 400, 700])
+def test_banded_column_classes(k_mean):
+    # spans every register class (<=32, 64, 128, 256, 512 entries) and the
+    # streaming path (> 512), with ragged column lengths
+    n_dom = max(3 * k_mean, 60)
+    m = banded_imdp(n_dom, 2, n_dom * 2 * (k_mean + 1) + 1, eps=0.08, seed=k_mean)
+    model = _model(m)
+    for pess, maxi in [(True, True), (False, False)]:
+        _compare(m, model, horizon=15, reach=m.goal, pessimistic=pess, maximize=maxi)
+
+
+def test_reach_avoid():
+    m = banded_imdp(400, 3, 400 * 3 * 13 + 1, eps=0.1, seed=8)
+    model = _model(m)
+    avoid = np.concatenate([m.sink, np.arange(0, 20)])
+    for pess, maxi in MODES:
+        _compare(m, model, property=oracle.REACH_AVOID, horizon=30, reach=m.goal, avoid=avoid,
+                 pessimistic=pess, maximize=maxi)
+
+
+@pytest.mark.parametrize("pess", [True, False])
+def test_infinite_horizon(pess):
+    m = banded_imdp(300, 2, 300 * 2 * 16 + 1, eps=0.05, seed=9)
+    model = _model(m)
+    V, k, res, pol, oV = _compare(m, model, policy=True, infinite_time=True, eps=1e-7, horizon=100000,
+                                  reach=m.goal, pessimistic=pess)
+    assert np.max(np.abs(res)) < 1e-7
+    check_policy_row(m, V - res, pol[0], set(m.goal.tolist()), pess, True)
+
+
+def test_infinite_horizon_cap_reports_noconv():
+    m = banded_imdp(200, 1, 200 * 10 + 1, seed=10)
+    model = _model(m)
+    st, V, k, res, _ = g.value_iteration(model, m.n_states, infinite_time=True, eps=1e-300, horizon=7, reach=m.goal)
+    assert st == "enoconv" and k == 7
+    ost, oV, ok, _, _ = run_oracle(m, infinite_time=True, eps=1e-300, horizon=7, reach=m.goal)
+    np.testing.assert_allclose(V, oV, atol=TOL_F64)
+
+
+def test_time_dependent_policy_all_rows():
+    m = random_imdp(25, max_actions=3, density=0.4, seed=77)
+    model = _model(m)
+    K = 6
+    st, V, k, res, pol = g.value_iteration(model, m.n_states, policy=True, horizon=K, reach=m.goal)
+    for t in range(K):
+        # row t is the decision of iteration K - t, made from V_{K-t-1}
+        _, Vp, _, _, _ = run_oracle(m, horizon=K - t - 1, reach=m.goal)
+        check_policy_row(m, Vp, pol[t], set(m.goal.tolist()), True, True)
+
+
+# --------------------------------------------------------------------------- batch vs alone, device buffers
+
+def test_batch_equals_alone_bitwise():
+    import torch
+    ms = [banded_imdp(120, 2, 120 * 2 * 9 + 1, seed=s) for s in range(3)] + [random_imdp(30, seed=4)]
+    models = [_model(m) for m in ms]
+    specs = [g.make_spec(horizon=10 + 5 * i, reach=m.goal, pessimistic=(i % 2 == 0), maximize=(i < 2))
+             for i, m in enumerate(ms)]
+    outs = [np.zeros(m.n_states) for m in ms]
+    ks = [0] * len(ms)
+    g.imdp_value_iteration_batch(models, specs, outs, ks)
+    for i, m in enumerate(ms):
+        alone = np.zeros(m.n_states)
+        kk = [0]
+        g.imdp_value_iteration(models[i], specs[i], alone, kk)
+        assert kk[0] == ks[i] == 10 + 5 * i
+        np.testing.assert_array_equal(outs[i], alone)
+        _, oV, _, _, _ = run_oracle(m, horizon=10 + 5 * i, reach=m.goal, pessimistic=(i % 2 == 0), maximize=(i < 2))
+        np.testing.assert_allclose(alone, oV, atol=TOL_F64)
+    # device output buffers give the same numbers
+    dev = torch.zeros(ms[0].n_states, dtype=torch.float64, device="cuda")
+    g.imdp_value_iteration(models[0], specs[0], dev)
+    np.testing.assert_array_equal(dev.cpu().numpy(), outs[0])
+
+
+def test_device_inputs():
+    import torch
+    m = banded_imdp(200, 2, 200 * 2 * 12 + 1, seed=12)
+    t = {k: torch.from_numpy(np.ascontiguousarray(getattr(m, k))).cuda()
+         for k in ("stateptr", "colptr", "rowval", "lower", "upper")}
+    model = g.imdp_create_csc(m.n_states, m.n_cols, m.nnz, t["stateptr"], t["colptr"], t["rowval"], t["lower"],
+                              t["upper"])
+    host_model = _model(m)
+    a = g.value_iteration(model, m.n_states, horizon=10, reach=m.goal)[1]
+    b = g.value_iteration(host_model, m.n_states, horizon=10, reach=m.goal)[1]
+    np.testing.assert_array_equal(a, b)
+
+
+def test_dense_create_matches_csc(worked_example):
+    ex = worked_example
+    n = ex["n_states"]
+    m_cols = len(ex["colptr"]) - 1
+    lo = np.zeros((m_cols, n)); up = np.zeros((m_cols, n))
+    for j in range(m_cols):
+        for i in range(ex["colptr"][j], ex["colptr"][j + 1]):
+            lo[j, ex["rowval"][i]] = ex["lower"][i]; up[j, ex["rowval"][i]] = ex["upper"][i]
+    acts = np.diff(ex["stateptr"]).astype(np.int32)
+    dm = g.imdp_create_dense(n, acts, np.ascontiguousarray(lo.reshape(-1)), np.ascontiguousarray(up.reshape(-1)))
+    class M: pass
+    m = M()
+    for key in ("n_states", "stateptr", "colptr", "rowval", "lower", "upper"):
+        setattr(m, key, ex[key])
+    cm = _model(m)
+    for K in (1, 5, 30):
+        a = g.value_iteration(dm, n, horizon=K, reach=ex["goal"])[1]
+        b = g.value_iteration(cm, n, horizon=K, reach=ex["goal"])[1]
+        np.testing.assert_array_equal(a, b)
+
+
+# --------------------------------------------------------------------------- errors
+
+def test_rejects_infeasible_and_malformed():
+    m = random_imdp(6, seed=1)
+    bad = m.lower.copy(); bad[0] = m.upper[0] + 0.1
+    with pytest.raises(g.ImdpError) as e:
+        g.imdp_create_csc(m.n_states, m.n_cols, m.nnz, m.stateptr, m.colptr, m.rowval, bad, m.upper)
+    assert e.value.status == g.IMDP_EINFEASIBLE
+    rows = m.rowval.copy(); rows[0] = 99
+    with pytest.raises(g.ImdpError) as e:
+        g.imdp_create_csc(m.n_states, m.n_cols, m.nnz, m.stateptr, m.colptr, rows, m.lower, m.upper)
+    assert e.value.status == g.IMDP_EINVAL
+    model = _model(m)
+    with pytest.raises(g.ImdpError):
+        g.value_iteration(model, m.n_states, horizon=3, reach=[100])
+    with pytest.raises(g.ImdpError):
+        g.value_iteration(model, m.n_states, property=g.IMDP_REACH_AVOID, horizon=3, reach=[1], avoid=[1])
+
+
+# --------------------------------------------------------------------------- full-size shapes, sampled outputs
+
+@pytest.mark.parametrize("name", ["cartpole3840", "pimdp2"])
+def test_full_size_sampled_one_step(name):
+    """At the benchmark's full sizes: the last Bellman step of a K = 200 run,
+    recomputed by the oracle state by state from the GPU's V_{K-1}."""
+    m = make_config(name)
+    model = _model(m)
+    K = 200
+    st, V, k, res, pol = g.value_iteration(model, m.n_states, policy=True, horizon=K, reach=m.goal)
+    assert st == "ok" and k == K
+    assert np.all(V >= 0) and np.all(V <= 1) and np.all(res >= 0)
+    Vprev = V - res
+    rng = np.random.default_rng(0)
+    goal = set(m.goal.tolist())
+    for s in rng.choice(m.n_states, 64, replace=False):
+        if s in goal:
+            assert V[s] == 1.0 and pol[0][s] == -1
+            continue
+        qs = []
+        for j in range(m.stateptr[s], m.stateptr[s + 1]):
+            a, b = m.colptr[j], m.colptr[j + 1]
+            qs.append(oracle.omax_column(Vprev[m.rowval[a:b]], m.lower[a:b], m.upper[a:b], True)[0])
+        assert abs(V[s] - max(qs)) <= 1e-12, (s, V[s], qs)
+        assert abs(qs[pol[0][s]] - max(qs)) <= 1e-12
