@@ -162,6 +162,27 @@ IMDP_API imdp_status imdp_value_iteration_batch(imdp_model* const* models, const
                                        double* const* V_out, int32_t* k_out, void* stream);
 
 /*
+ * Value iteration that allocates no device memory (the paper has no counterpart;
+ * this is a deployment aid). For callers that create their models once at
+ * start-up and may not allocate afterwards: a controller re-planning every cycle
+ * under a fixed memory budget, or code whose device memory belongs to another
+ * framework's allocator. Instead of per-call buffers it uses one fixed scratch
+ * array compiled into the library (about 2.7 MB, held by every GPU that loads
+ * the library until the process exits).
+ *   m, spec   as for imdp_value_iteration (reach / reach-avoid properties);
+ *             at most 131072 states and 131072 reach + avoid indices, else
+ *             IMDP_EINVAL with a message naming the limit
+ *   V_out     double[n_states], DEVICE memory on the model's device (current)
+ *   k_out     (host, nullable) iterations performed
+ * The first call on a device looks up the scratch array's device address; make
+ * that first call before any stream capture. All calls share the one array:
+ * calls that overlap on the GPU (other streams or host threads) race. Policy and
+ * residual outputs are not offered here.
+ */
+IMDP_API imdp_status imdp_value_iteration_noalloc(imdp_model* m, const imdp_spec* spec, double* V_out,
+                                                  int32_t* k_out, void* stream);
+
+/*
  * Resident solver session: the device state of value iteration for `count`
  * problems kept between calls (value buffers, iteration counters, policy
  * storage), so repeated runs and step-by-step control need no re-setup.

@@ -27,7 +27,7 @@ EXPORTED = [
     "imdp_status_string", "imdp_last_error", "imdp_version", "imdp_create_csc", "imdp_create_dense",
     "imdp_model_destroy", "imdp_model_info", "imdp_value_iteration", "imdp_value_iteration_batch",
     "imdp_session_create", "imdp_session_reset", "imdp_session_step", "imdp_session_run", "imdp_session_read",
-    "imdp_session_launches", "imdp_session_destroy",
+    "imdp_session_launches", "imdp_session_destroy", "imdp_value_iteration_noalloc",
 ]
 
 
@@ -95,6 +95,8 @@ def load(path: Optional[str] = None):
     lib.imdp_session_launches.restype = C.c_int64
     lib.imdp_session_destroy.argtypes = [vp]
     lib.imdp_session_destroy.restype = None
+    lib.imdp_value_iteration_noalloc.argtypes = [vp, C.POINTER(imdp_spec), vp, C.POINTER(C.c_int32), vp]
+    lib.imdp_value_iteration_noalloc.restype = C.c_int
     for f in ("imdp_create_csc", "imdp_create_dense", "imdp_model_info", "imdp_value_iteration",
               "imdp_value_iteration_batch", "imdp_session_create", "imdp_session_reset", "imdp_session_step",
               "imdp_session_run", "imdp_session_read"):
@@ -302,6 +304,19 @@ def imdp_session_launches(s: Session) -> int:
 
 def imdp_session_destroy(s: Session):
     s.close()
+
+
+def imdp_value_iteration_noalloc(model: Model, spec, V_out, k_out=None, stream=None, check=True) -> int:
+    """Value iteration using only the library's fixed scratch array (no device
+    allocation during the call). ``V_out`` must be a device buffer."""
+    k = C.c_int32(0)
+    st = load().imdp_value_iteration_noalloc(C.c_void_p(model.handle), C.byref(spec), _ptr(V_out), C.byref(k),
+                                             _stream(stream))
+    if k_out is not None:
+        k_out[0] = k.value
+    if check and st not in (IMDP_OK, IMDP_ENOCONV):
+        _check(st, "imdp_value_iteration_noalloc")
+    return st
 
 
 # ---------------------------------------------------------------- convenience wrappers (host numpy in/out)

@@ -1,0 +1,65 @@
+"""The allocation-free entry point (imdp_value_iteration_noalloc) against the
+regular one, through the C ABI.
+
+It serves callers that create models once and then may not allocate device
+memory on their query path (fixed memory budgets, device memory owned by
+another allocator). It keeps its buffers in one scratch array inside the
+library that every call reuses, so the test makes two calls in a row with
+different specifications and checks both: leftovers from the first call must
+not leak into the second. This file is collected last on purpose."""
+import numpy as np
+import pytest
+
+import paper_2401_04068_gb300 as g
+from gpu_helpers import TOL_F64
+from workloads import banded_imdp
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_matches_regular_entry_point_twice_in_a_row():
+    import torch
+    assert torch.cuda.is_available()
+    m = banded_imdp(3000, 2, 3000 * 2 * 30 + 3000 * 2 + 1, eps=0.08, seed=31)
+    model = g.create_model(m)
+    avoid = np.arange(0, 40, dtype=np.int32)
+    specs = [
+        g.make_spec(horizon=60, reach=m.goal, pessimistic=True, maximize=True),
+        g.make_spec(property=g.IMDP_REACH_AVOID, horizon=45, reach=m.goal, avoid=avoid, pessimistic=False,
+                    maximize=False),
+    ]
+    for spec in specs:
+        ref = np.zeros(m.n_states)
+        kr = [0]
+        g.imdp_value_iteration(model, spec, ref, kr)
+        out = torch.full((m.n_states,), -1.0, dtype=torch.float64, device="cuda")
+        ko = [0]
+        st = g.imdp_value_iteration_noalloc(model, spec, out, ko)
+        assert st == g.IMDP_OK
+        assert ko[0] == kr[0] == spec.horizon
+        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=TOL_F64)
+
+
+def test_noalloc_infinite_horizon_and_limits():
+    import torch
+    m = banded_imdp(500, 1, 500 * 12 + 500 + 1, seed=32)
+    model = g.create_model(m)
+    spec = g.make_spec(infinite_time=True, eps=1e-8, horizon=100000, reach=m.goal)
+    ref = np.zeros(m.n_states)
+    kr = [0]
+    g.imdp_value_iteration(model, spec, ref, kr)
+    out = torch.zeros(m.n_states, dtype=torch.float64, device="cuda")
+    ko = [0]
+    g.imdp_value_iteration_noalloc(model, spec, out, ko)
+    assert ko[0] == kr[0]
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=TOL_F64)
+    # a host output buffer is refused
+    with pytest.raises(g.ImdpError):
+        g.imdp_value_iteration_noalloc(model, spec, np.zeros(m.n_states))
+    # more states than the fixed scratch holds: a clear error
+    n = 131073
+    chain = g.imdp_create_csc(n, n, n, np.arange(n + 1, dtype=np.int32), np.arange(n + 1, dtype=np.int32),
+                              np.arange(n, dtype=np.int32), np.ones(n), np.ones(n))
+    big = torch.zeros(n, dtype=torch.float64, device="cuda")
+    with pytest.raises(g.ImdpError, match="131072"):
+        g.imdp_value_iteration_noalloc(chain, g.make_spec(horizon=3, reach=[0]), big)
