@@ -165,12 +165,14 @@ def cpu_baseline(m, horizon: int, budget_s: float = 12.0, sample_models: int = N
                                  m.lower[:e_end], m.upper[:e_end]), e_end
 
     if n_models > 1:
-        # calibrate on one model, then size the sample to the budget
-        om1, nz1 = sub(1)
-        goal1 = m.goal[m.goal < offs[1]]
+        # calibrate on a few models (enough to occupy every thread), then size the
+        # sample to the budget
+        nc = min(n_models, max(4 * cores, 16))
+        omc, _ = sub(nc)
+        goalc = m.goal[m.goal < offs[nc]]
         t = time.perf_counter()
-        oracle.value_iteration(om1, oracle.OracleSpec(horizon=horizon, reach=goal1), threads=cores)
-        dt = max(time.perf_counter() - t, 1e-4)
+        oracle.value_iteration(omc, oracle.OracleSpec(horizon=horizon, reach=goalc), threads=cores)
+        dt = max(time.perf_counter() - t, 1e-4) / nc
         nm = sample_models or int(max(1, min(n_models, budget_s / dt)))
         om, nz = sub(nm)
         goal = m.goal[m.goal < offs[nm]]
@@ -352,7 +354,7 @@ def main():
     ap.add_argument("--horizon", type=int, default=200)
     ap.add_argument("--models", type=int, default=0, help="override the number of models of a batch workload")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--ref-budget", type=float, default=12.0)
+    ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 1)

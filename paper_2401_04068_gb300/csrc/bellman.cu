@@ -1,29 +1,45 @@
 // Robust Bellman step (Eq. 2 / Eq. 3) with O-maximization (Sec. 4) for sm_103a.
 //
 // One launch performs one value-iteration step V_{k-1} -> V_k for every problem
-// of a batch that is still running. A warp owns one state at a time and walks
-// its actions (the CSC columns of that state); the optimum over actions, the
-// target/avoid mask, the policy record and the residual are fused in.
+// of a batch that is still running.
+//
+// Data movement. The launch is persistent (one CTA per SM). The model is cut into
+// state-aligned tiles (consecutive states of one problem, <= kTileEntries
+// entries). A producer warp streams each tile's destination indices and bound
+// pairs into a two-stage shared-memory ring with bulk asynchronous copies
+// (cp.async.bulk, completion counted on an mbarrier), while eight consumer warps
+// work on the previous tile. Every entry crosses HBM once per iteration.
 //
 // O-maximization without a sort. For a pessimistic adversary the procedure of
 // Sec. 4 orders the destinations by ascending V, starts from p = lower and hands
 // out rem = 1 - sum(lower) gap by gap along that order. Its result depends only
-// on the *threshold*: the first destination (in that order) at which the
-// inclusive prefix of gaps reaches rem. Everything before it receives its full
-// gap, the threshold receives what is left, everything after it keeps its lower
-// bound. Destinations with equal V are interchangeable (the value of the sum is
-// the same whichever of them gets the mass), so the threshold can be taken on
-// the value itself:
+// on the threshold: the first destination (in that order) at which the inclusive
+// prefix of gaps reaches rem. Everything before it receives its full gap, the
+// threshold receives what is left, everything after it keeps its lower bound.
+// Destinations with equal V are interchangeable (the sum is the same whichever of
+// them gets the mass), so
 //     q = sum_i V_i P_lo,i + sum_{V_i < v*} V_i gap_i + v* (rem - sum_{V_i < v*} gap_i),
 //     v* = the smallest V_i with sum_{V_j <= V_i} gap_j >= rem.
-// The kernel finds v* by a weighted selection on integer keys (the Q1.63 value,
-// complemented for an optimistic adversary so that the order is always
-// ascending): each round takes the min/max key of the remaining candidates,
-// histograms their gaps into 32 bins of the key range, and keeps the bin in
-// which the prefix crosses rem. Each round shrinks the key range by >= 16x and
-// usually isolates a single key after two or three rounds; no element moves.
-// A final pass applies the threshold and forms the dot product.
+// Keys are the Q1.63 values (complemented for an optimistic adversary so that the
+// order is always ascending). A consumer warp handles one column at a time:
+//   1. gathers V for the column, stores the keys in shared memory and takes the
+//      min/max key (redux.sync on 32-bit halves);
+//   2. histograms the gaps (and counts) into 64 bins of [min, max] and scans the
+//      bins: the bin where the prefix crosses rem holds the threshold, entries in
+//      lower bins are fully "below";
+//   3. compacts the entries of that bin (usually one to a few) into a list of at
+//      most 32 and resolves them exactly: each takes its gap, clipped to what the
+//      entries before it in (key, position) order leave of rem.
+// A crossing bin with more than 32 entries is narrowed by further rounds over its
+// key range; a bin whose entries share one key is resolved as a group. Sums are
+// exact 64-bit integer sums, so results do not depend on the order in which lanes
+// or bins are combined. After all columns of a tile, the consumer threads take
+// the optimum over each state's actions, apply the reach/avoid mask and write V,
+// the policy and the residual.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstddef>
 
 #include "imdp_internal.h"
 
@@ -32,330 +48,513 @@ namespace imdp {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBins = 64;
+constexpr int kConsumerWarps = 8;
+constexpr int kStages = 2;
+constexpr int kBlockThreads = 32 * (kConsumerWarps + 1);
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz: bound of every wait
 
-__device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    uint64_t y = __shfl_xor_sync(kFull, x, o);
-    x = y < x ? y : x;
-  }
-  return x;
-}
-__device__ __forceinline__ uint64_t warp_max_u64(uint64_t x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    uint64_t y = __shfl_xor_sync(kFull, x, o);
-    x = y > x ? y : x;
-  }
-  return x;
-}
-__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-  return x;
-}
-__device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t x, int lane) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint64_t y = __shfl_up_sync(kFull, x, o);
-    if (lane >= o) x += y;
-  }
-  return x;
-}
-
-// Result of the threshold search over one column.
-struct Threshold {
-  uint64_t key;   // threshold key; ~0 when the gaps cannot absorb rem (all below)
-  uint64_t fb;    // sum of gaps of entries with key < threshold
-  bool all_below;
+struct WarpScratch {
+  unsigned int hl[kBins];        // gap sum per bin, low 32 bits (wraps)
+  unsigned int hh[kBins];        // gap sum per bin, high 32 bits plus the low part's carries
+  unsigned int hc[kBins];        // entry count per bin
+  unsigned int _pad[kBins];
+  unsigned long long ck[32];     // compacted candidates: key
+  unsigned long long cg[32];     //                       gap
 };
 
-// One selection round's bookkeeping shared by the register and streaming paths.
-// Given the warp-wide min/max of the candidate keys and the per-lane histogram
-// value h (bin = lane), decide the next window. Returns true when done.
-__device__ __forceinline__ bool select_round_finish(uint64_t h, int lane, uint64_t rem, uint64_t cmin, int shift,
-                                                    uint64_t cmax, uint64_t& fb, uint64_t& lo, uint64_t& hi,
-                                                    bool& all_below) {
-  uint64_t incl = warp_incl_scan_u64(h, lane);
-  unsigned cross = __ballot_sync(kFull, fb + incl >= rem);
-  if (cross == 0) {  // only possible in the first round: sum of all gaps < rem
-    all_below = true;
-    return true;
-  }
-  int b = __ffs(cross) - 1;
-  uint64_t excl_b = __shfl_sync(kFull, incl - h, b);
-  fb += excl_b;
-  lo = cmin + ((uint64_t)b << shift);
-  uint64_t top = lo + ((1ull << shift) - 1ull);
-  hi = top < cmax ? top : cmax;
-  return false;
+// One ring stage: a tile's data and metadata, each array a 16-byte-aligned
+// bulk-copy window (so its first element may sit a few slots in).
+struct Stage {
+  int32_t rows[kTileEntries + 8];        // destinations
+  ulonglong2 lg[kTileEntries];           // {lower, gap}
+  unsigned long long keys[kTileEntries]; // keys of the running iteration
+  unsigned long long q[kTileCols];       // per-column O-maximization values
+  unsigned long long rem[kTileCols + 4]; // 1 - sum(lower) per column
+  int32_t sptr[kTileStates + 8];         // stateptr window
+  int32_t cptr[kTileCols + 8];           // colptr window
+  uint8_t fixed[kTileStates + 32];       // reach/avoid mask window
+  Problem prob;                          // descriptor of the tile's problem
+  int32_t active;                        // set by the producer: the problem still runs
+  int32_t k_iter;                        //                      iteration being computed
+  int32_t fixed_off;                     //                      offset of state s0 in `fixed`
+  int32_t _pad;
+};
+
+struct Smem {
+  Stage st[kStages];
+  WarpScratch ws[kConsumerWarps];
+  unsigned long long full[kStages];
+  unsigned long long empty[kStages];
+  int is_last;
+  volatile int go;
+};
+static_assert(sizeof(int32_t) * (kTileEntries + 8) % 16 == 0, "lg must stay 16-byte aligned");
+static_assert(offsetof(Stage, rem) % 16 == 0 && offsetof(Stage, sptr) % 16 == 0 && offsetof(Stage, cptr) % 16 == 0 &&
+                  offsetof(Stage, fixed) % 16 == 0 && offsetof(Stage, prob) % 16 == 0 && sizeof(Problem) % 16 == 0,
+              "bulk-copy destinations must be 16-byte aligned");
+static_assert(sizeof(Stage) % 16 == 0, "stage alignment");
+static_assert(sizeof(Smem) <= 232448, "shared memory budget of one CTA");
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * kConsumerWarps) : "memory");
 }
 
-// Column held in registers: up to 32*E entries, entry idx = lane + 32*e.
-template <int E>
-__device__ __forceinline__ uint64_t column_q_regs(const int32_t* __restrict__ rowval,
-                                                  const ulonglong2* __restrict__ lg, int32_t c0, int32_t k,
-                                                  uint64_t rem, const uint64_t* __restrict__ V, bool pess,
-                                                  unsigned long long* hist, int lane) {
-  uint64_t key[E], lo_[E], gap[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    int idx = lane + 32 * e;
-    if (idx < k) {
-      int32_t r = __ldg(rowval + c0 + idx);
-      ulonglong2 p = __ldg(lg + c0 + idx);
-      uint64_t v = __ldg(V + r);
-      key[e] = pess ? v : (kOne - v);
-      lo_[e] = p.x;
-      gap[e] = p.y;
-    } else {
-      key[e] = ~0ull;  // never a candidate, never below a finite threshold
-      lo_[e] = 0;
-      gap[e] = 0;
+// Wait for phase `parity` of an mbarrier, giving up after kWaitCycles or when
+// another thread has flagged an error (unless `drain`). Returns false on give-up.
+__device__ bool wait_phase(unsigned long long* bar, uint32_t parity, unsigned* err, bool drain) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (!drain && *(volatile unsigned*)err) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      atomicExch(err, 1u);
+      return false;
     }
   }
-
-  uint64_t thr = ~0ull, fb = 0;
-  bool all_below = false;
-  if (rem != 0) {
-    uint64_t lo = 0, hi = kOne;
-    for (int round = 0; round < 20; ++round) {
-      uint64_t cmin = ~0ull, cmax = 0;
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        bool c = key[e] >= lo && key[e] <= hi;
-        if (c) {
-          cmin = key[e] < cmin ? key[e] : cmin;
-          cmax = key[e] > cmax ? key[e] : cmax;
-        }
-      }
-      cmin = warp_min_u64(cmin);
-      cmax = warp_max_u64(cmax);
-      if (cmin > cmax) {  // no candidate at all (cannot happen for a feasible column)
-        all_below = true;
-        break;
-      }
-      if (cmin == cmax) {
-        thr = cmin;
-        break;
-      }
-      int bits = 64 - __clzll((long long)(cmax - cmin));
-      int shift = bits > 5 ? bits - 5 : 0;
-      hist[lane] = 0;
-      __syncwarp();
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        if (key[e] >= cmin && key[e] <= cmax && key[e] >= lo && key[e] <= hi && gap[e] != 0)
-          atomicAdd(&hist[(key[e] - cmin) >> shift], (unsigned long long)gap[e]);
-      }
-      __syncwarp();
-      uint64_t h = hist[lane];
-      __syncwarp();
-      if (select_round_finish(h, lane, rem, cmin, shift, cmax, fb, lo, hi, all_below)) break;
-    }
-    if (all_below) thr = ~0ull;
-  }
-  // rem == 0: every entry keeps its lower bound; thr stays ~0 but nothing is
-  // "below" in the sense of receiving a gap, handled by the rem test.
-
-  uint64_t acc = 0;
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    if (key[e] != ~0ull) {
-      uint64_t v = pess ? key[e] : (kOne - key[e]);
-      uint64_t w = (rem != 0 && key[e] < thr) ? lo_[e] + gap[e] : lo_[e];
-      acc += __umul64hi(v, w);
-    }
-  }
-  acc = warp_sum_u64(acc);
-  if (rem != 0 && !all_below) {
-    uint64_t vthr = pess ? thr : (kOne - thr);
-    acc += __umul64hi(vthr, rem - fb);
-  }
-  return acc;  // Q2.62
 }
 
-// Column too long for registers: the same rounds, re-reading the column from
-// global memory (L1/L2) on every pass, one entry per lane per step.
-__device__ uint64_t column_q_stream(const int32_t* __restrict__ rowval, const ulonglong2* __restrict__ lg,
-                                    int32_t c0, int32_t k, uint64_t rem, const uint64_t* __restrict__ V, bool pess,
-                                    unsigned long long* hist, int lane) {
-  auto load_key = [&](int idx) -> uint64_t {
-    uint64_t v = __ldg(V + __ldg(rowval + c0 + idx));
+// ---------------------------------------------------------------- warp reductions
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
+  const unsigned hi = __reduce_min_sync(kFull, (unsigned)(x >> 32));
+  const unsigned lo = __reduce_min_sync(kFull, ((unsigned)(x >> 32) == hi) ? (unsigned)x : 0xffffffffu);
+  return ((uint64_t)hi << 32) | lo;
+}
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t x) {
+  const unsigned hi = __reduce_max_sync(kFull, (unsigned)(x >> 32));
+  const unsigned lo = __reduce_max_sync(kFull, ((unsigned)(x >> 32) == hi) ? (unsigned)x : 0u);
+  return ((uint64_t)hi << 32) | lo;
+}
+// Exact 64-bit warp sum from three 22/22/20-bit partial sums (no carries lost).
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
+  const unsigned a = __reduce_add_sync(kFull, (unsigned)(x & 0x3fffffu));
+  const unsigned b = __reduce_add_sync(kFull, (unsigned)((x >> 22) & 0x3fffffu));
+  const unsigned c = __reduce_add_sync(kFull, (unsigned)(x >> 44));
+  return (uint64_t)a + ((uint64_t)b << 22) + ((uint64_t)c << 44);
+}
+__device__ __forceinline__ uint64_t warp_excl_scan_u64(uint64_t x, int lane) {
+  uint64_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  return incl - x;
+}
+
+// ---------------------------------------------------------------- one column
+
+// Entries [0, k) of one column: destinations `rows`, bound pairs `lg`, key
+// scratch `keys` (shared memory; nullptr = recompute keys from V on every pass,
+// used when the column is read straight from global memory). Returns q in Q2.62.
+__device__ uint64_t column_q(const int32_t* rows, const ulonglong2* lg, unsigned long long* keys, int32_t k,
+                             uint64_t rem, const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane) {
+  auto key_of = [&](int idx) -> uint64_t {
+    if (keys) return keys[idx];
+    const uint64_t v = __ldg(V + rows[idx]);
     return pess ? v : (kOne - v);
   };
-  uint64_t thr = ~0ull, fb = 0;
-  bool all_below = false;
+  // 1. keys and their range
+  uint64_t lmin = ~0ull, lmax = 0;
+#pragma unroll 4
+  for (int idx = lane; idx < k; idx += 32) {
+    const uint64_t v = __ldg(V + rows[idx]);
+    const uint64_t key = pess ? v : (kOne - v);
+    if (keys) keys[idx] = key;
+    lmin = key < lmin ? key : lmin;
+    lmax = key > lmax ? key : lmax;
+  }
+  __syncwarp();
+
+  // 2. threshold search: after it, keys < lo are below (full gap), keys > hi are
+  // above (lower bound), keys in [lo, hi] are candidates sharing rem - fb.
+  uint64_t lo = 0, hi = 0, fb = 0;
+  bool all_below = false, uniform = true;  // rem == 0: every entry keeps its lower bound
   if (rem != 0) {
-    uint64_t lo = 0, hi = kOne;
-    for (int round = 0; round < 20; ++round) {
-      uint64_t cmin = ~0ull, cmax = 0;
-      for (int idx = lane; idx < k; idx += 32) {
-        uint64_t key = load_key(idx);
-        if (key >= lo && key <= hi) {
-          cmin = key < cmin ? key : cmin;
-          cmax = key > cmax ? key : cmax;
-        }
-      }
-      cmin = warp_min_u64(cmin);
-      cmax = warp_max_u64(cmax);
-      if (cmin > cmax) {  // no candidate at all (cannot happen for a feasible column)
+    uniform = false;
+    uint64_t cmin = warp_min_u64(lmin), cmax = warp_max_u64(lmax);
+    lo = 0;
+    hi = kOne;
+    for (int round = 0; round < 12; ++round) {
+      if (cmin > cmax) {  // no entry: nothing absorbs rem
         all_below = true;
         break;
       }
-      if (cmin == cmax) {
-        thr = cmin;
+      if (cmin == cmax) {  // the candidates share one key
+        lo = hi = cmin;
+        uniform = true;
         break;
       }
-      int bits = 64 - __clzll((long long)(cmax - cmin));
-      int shift = bits > 5 ? bits - 5 : 0;
-      hist[lane] = 0;
+      const int bits = 64 - __clzll((long long)(cmax - cmin));
+      const int shift = bits > 6 ? bits - 6 : 0;
+      ws->hl[lane] = 0;
+      ws->hl[lane + 32] = 0;
+      ws->hh[lane] = 0;
+      ws->hh[lane + 32] = 0;
+      ws->hc[lane] = 0;
+      ws->hc[lane + 32] = 0;
       __syncwarp();
       for (int idx = lane; idx < k; idx += 32) {
-        uint64_t key = load_key(idx);
+        const uint64_t key = key_of(idx);
         if (key >= lo && key <= hi) {
-          uint64_t g = __ldg(lg + c0 + idx).y;
-          if (g) atomicAdd(&hist[(key - cmin) >> shift], (unsigned long long)g);
+          const int b = (int)((key - cmin) >> shift);
+          const uint64_t g = lg[idx].y;
+          // exact 64-bit bin sums from native 32-bit atomics: the adder whose
+          // low-word addition wraps carries one into the high word
+          const unsigned gl = (unsigned)g;
+          const unsigned old = atomicAdd(&ws->hl[b], gl);
+          const unsigned up = (unsigned)(g >> 32) + ((old + gl) < old ? 1u : 0u);
+          if (up) atomicAdd(&ws->hh[b], up);
+          atomicAdd(&ws->hc[b], 1u);
         }
       }
       __syncwarp();
-      uint64_t h = hist[lane];
+      const uint64_t h0 = ((uint64_t)ws->hh[2 * lane] << 32) | ws->hl[2 * lane];
+      const uint64_t h1 = ((uint64_t)ws->hh[2 * lane + 1] << 32) | ws->hl[2 * lane + 1];
+      const uint64_t ex = warp_excl_scan_u64(h0 + h1, lane);
+      const uint64_t i0 = fb + ex + h0, i1 = i0 + h1;
+      const unsigned cross = __ballot_sync(kFull, i1 >= rem);
+      if (cross == 0) {  // first round only: the gaps cannot absorb rem
+        all_below = true;
+        break;
+      }
+      const int L = __ffs(cross) - 1;
+      const bool first = i0 >= rem;
+      const int b = __shfl_sync(kFull, first ? 2 * lane : 2 * lane + 1, L);
+      fb = __shfl_sync(kFull, first ? fb + ex : i0, L);
+      const unsigned cnt = ws->hc[b];
       __syncwarp();
-      if (select_round_finish(h, lane, rem, cmin, shift, cmax, fb, lo, hi, all_below)) break;
+      lo = cmin + ((uint64_t)b << shift);
+      const uint64_t top = lo + ((1ull << shift) - 1ull);
+      hi = top < cmax ? top : cmax;
+      if (cnt <= 32) break;
+      // narrow to the min/max of the crossing bin's entries
+      uint64_t a = ~0ull, z = 0;
+      for (int idx = lane; idx < k; idx += 32) {
+        const uint64_t key = key_of(idx);
+        if (key >= lo && key <= hi) {
+          a = key < a ? key : a;
+          z = key > z ? key : z;
+        }
+      }
+      cmin = warp_min_u64(a);
+      cmax = warp_max_u64(z);
     }
-    if (all_below) thr = ~0ull;
   }
-  uint64_t acc = 0;
-  for (int idx = lane; idx < k; idx += 32) {
-    uint64_t key = load_key(idx);
-    ulonglong2 p = __ldg(lg + c0 + idx);
-    uint64_t v = pess ? key : (kOne - key);
-    uint64_t w = (rem != 0 && key < thr) ? p.x + p.y : p.x;
-    acc += __umul64hi(v, w);
+
+  // 3. final pass: lower bounds everywhere, full gaps below the candidates,
+  // candidates compacted (or summed when they share one key).
+  uint64_t acc = 0, gsum = 0;
+  unsigned pos = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int base = 0; base < k; base += 32) {
+    const int idx = base + lane;
+    const bool valid = idx < k;
+    uint64_t key = 0;
+    ulonglong2 b = make_ulonglong2(0, 0);
+    if (valid) {
+      key = key_of(idx);
+      b = lg[idx];
+    }
+    const bool below = all_below || key < lo;
+    const bool cand = valid && !all_below && key >= lo && key <= hi;
+    if (valid) acc += __umul64hi(pess ? key : (kOne - key), below ? b.x + b.y : b.x);
+    if (!uniform) {
+      const unsigned m = __ballot_sync(kFull, cand);
+      if (cand) {
+        const unsigned at = pos + __popc(m & lt);
+        ws->ck[at] = key;
+        ws->cg[at] = b.y;
+      }
+      pos += __popc(m);
+    } else if (cand) {
+      gsum += b.y;
+    }
   }
   acc = warp_sum_u64(acc);
-  if (rem != 0 && !all_below) {
-    uint64_t vthr = pess ? thr : (kOne - thr);
-    acc += __umul64hi(vthr, rem - fb);
+  if (all_below || rem == 0) return acc;
+  const uint64_t r2 = rem - fb;  // > 0 by construction of the crossing bin
+  if (uniform) {
+    // one key for all candidates: they take min(r2, their total gap) together
+    const uint64_t g = warp_sum_u64(gsum);
+    return acc + __umul64hi(pess ? lo : (kOne - lo), g < r2 ? g : r2);
   }
-  return acc;
+  __syncwarp();
+  // Resolve the <= 32 candidates exactly: candidate i takes its gap clipped to
+  // what the candidates ordered before it (by key, then list position) leave.
+  uint64_t extra = 0;
+  if (lane < (int)pos) {
+    const uint64_t ki = ws->ck[lane], gi = ws->cg[lane];
+    uint64_t before = 0;
+    for (unsigned j = 0; j < pos; ++j) {
+      const uint64_t kj = ws->ck[j];
+      if (kj < ki || (kj == ki && j < (unsigned)lane)) before += ws->cg[j];
+    }
+    const uint64_t left = r2 > before ? r2 - before : 0;
+    extra = __umul64hi(pess ? ki : (kOne - ki), gi < left ? gi : left);
+  }
+  __syncwarp();
+  return acc + warp_sum_u64(extra);
 }
 
-__device__ __forceinline__ int find_problem(const int32_t* __restrict__ base, int count, int32_t g) {
-  int lo = 0, hi = count;  // base[lo] <= g < base[hi]
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (__ldg(base + mid) <= g) lo = mid; else hi = mid;
-  }
-  return lo;
+// ---------------------------------------------------------------- the step kernel
+
+__device__ __forceinline__ bool problem_active(const StepLaunch& L, int p, int32_t* k_iter) {
+  const IterState& it = L.its[p];
+  const Problem& P = L.probs[p];
+  *k_iter = it.iter + 1;
+  return !it.done && (P.infinite || *k_iter <= P.horizon);
 }
 
-template <int E>
-__global__ void __launch_bounds__(kThreads) bellman_step_kernel(StepLaunch L) {
-  __shared__ unsigned long long hist_all[kWarpsPerBlock][32];
-  __shared__ int is_last;
+// V, policy and residual of state s once its actions' values are known.
+__device__ __forceinline__ void finish_state(const Problem& P, int32_t s, int32_t k_iter, uint64_t vnew, int32_t best,
+                                             const uint64_t* __restrict__ Vin, uint64_t* __restrict__ Vout,
+                                             unsigned long long& dmax) {
+  Vout[s] = vnew;
+  if (P.policy_mode == 1)
+    P.policy[(size_t)(P.horizon - k_iter) * P.n_states + s] = best;
+  else if (P.policy_mode == 2)
+    P.policy[s] = best;
+  if (P.infinite) {
+    const uint64_t vold = Vin[s];
+    const uint64_t d = vnew > vold ? vnew - vold : vold - vnew;
+    dmax = d > dmax ? d : dmax;
+  }
+}
+
+__global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaunch L) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  unsigned long long* hist = hist_all[warp];
-  const int32_t n_warps = gridDim.x * kWarpsPerBlock;
+  unsigned* err = &L.ctl->error;
 
-  int cur_p = -1;
-  unsigned long long run_max = 0;  // residual max of cur_p seen by this warp
-
-  for (int32_t g = blockIdx.x * kWarpsPerBlock + warp; g < L.total_states; g += n_warps) {
-    const int p = L.count == 1 ? 0 : find_problem(L.state_base, L.count, g);
-    const Problem& P = L.probs[p];
-    const IterState& it = L.its[p];
-    if (it.done) continue;
-    const int32_t k_iter = it.iter + 1;
-    if (!P.infinite && k_iter > P.horizon) continue;
-    if (p != cur_p) {
-      if (cur_p >= 0 && run_max && lane == 0 && L.probs[cur_p].infinite)
-        atomicMax(&L.its[cur_p].resmax, run_max);
-      cur_p = p;
-      run_max = 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&S.full[s], 1);
+      mbar_init(&S.empty[s], kConsumerWarps);
     }
-    const int32_t s = g - (L.count == 1 ? 0 : __ldg(L.state_base + p));
-    const uint64_t* __restrict__ Vin = P.V[(k_iter - 1) & 1];
-    uint64_t* __restrict__ Vout = P.V[k_iter & 1];
-    const uint8_t fx = P.fixed ? P.fixed[s] : 0;
-    uint64_t vnew;
-    int32_t best = -1;
-    if (fx == 1) {
-      vnew = kOne;
-    } else if (fx == 2) {
-      vnew = 0;
-    } else {
-      const bool pess = P.pessimistic != 0;
-      const int32_t jb = __ldg(P.stateptr + s), je = __ldg(P.stateptr + s + 1);
-      uint64_t bestq = 0;
-      for (int32_t j = jb; j < je; ++j) {
-        const int32_t c0 = __ldg(P.colptr + j);
-        const int32_t kk = __ldg(P.colptr + j + 1) - c0;
-        const uint64_t rem = __ldg(P.rem + j);
-        uint64_t q;
-        if (kk <= 32 * E)
-          q = column_q_regs<E>(P.rowval, P.lg, c0, kk, rem, Vin, pess, hist, lane);
-        else
-          q = column_q_stream(P.rowval, P.lg, c0, kk, rem, Vin, pess, hist, lane);
-        const bool better = best < 0 || (P.maximize ? q > bestq : q < bestq);
-        if (better) {
-          bestq = q;
-          best = j - jb;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == kConsumerWarps) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int i = 0;
+      bool ok = true;
+      int pending_round[kStages];
+      for (int s = 0; s < kStages; ++s) pending_round[s] = -1;
+      for (int32_t t = blockIdx.x; t < L.n_tiles; t += gridDim.x, ++i) {
+        const int stage = i % kStages, round = i / kStages;
+        if (round > 0 && !wait_phase(&S.empty[stage], (round - 1) & 1, err, false)) {
+          ok = false;
+          break;
+        }
+        pending_round[stage] = -1;
+        const Tile T = L.tiles[t];
+        Stage& st = S.st[stage];
+        int32_t k_iter;
+        const bool act = problem_active(L, T.p, &k_iter);
+        st.active = act ? 1 : 0;
+        st.k_iter = k_iter;
+        if (act && !T.big) {
+          const Problem& P = L.probs[T.p];
+          // 16-byte-aligned windows of every array the tile needs
+          const int32_t eb = T.e0 & ~3, ee = (T.e1 + 3) & ~3;
+          const int32_t sb = T.s0 & ~3, se = (T.s1 + 4) & ~3;
+          const int32_t cb = T.c0 & ~3, ce = (T.c1 + 4) & ~3;
+          const int32_t mb = T.c0 & ~1, me = (T.c1 + 1) & ~1;
+          const uintptr_t f0 = (uintptr_t)(P.fixed + T.s0), fa = f0 & ~(uintptr_t)15;
+          const uintptr_t fe = ((uintptr_t)(P.fixed + T.s1) + 15) & ~(uintptr_t)15;
+          st.fixed_off = (int32_t)(f0 - fa);
+          const uint32_t rb = (uint32_t)(ee - eb) * 4u, gb = (uint32_t)(T.e1 - T.e0) * 16u;
+          const uint32_t sbytes = (uint32_t)(se - sb) * 4u, cbytes = (uint32_t)(ce - cb) * 4u;
+          const uint32_t mbytes = (uint32_t)(me - mb) * 8u, fbytes = (uint32_t)(fe - fa);
+          mbar_arrive_expect_tx(&S.full[stage], rb + gb + sbytes + cbytes + mbytes + fbytes + (uint32_t)sizeof(Problem));
+          bulk_g2s(&st.prob, &P, (uint32_t)sizeof(Problem), &S.full[stage]);
+          if (sbytes) bulk_g2s(st.sptr, P.stateptr + sb, sbytes, &S.full[stage]);
+          if (cbytes) bulk_g2s(st.cptr, P.colptr + cb, cbytes, &S.full[stage]);
+          if (mbytes) bulk_g2s(st.rem, P.rem + mb, mbytes, &S.full[stage]);
+          if (fbytes) bulk_g2s(st.fixed, (const void*)fa, fbytes, &S.full[stage]);
+          if (rb) bulk_g2s(st.rows, P.rowval + eb, rb, &S.full[stage]);
+          if (gb) bulk_g2s(st.lg, P.lg + T.e0, gb, &S.full[stage]);
+          pending_round[stage] = round;
+        } else {
+          mbar_arrive(&S.full[stage]);  // releases the plain stores above as well
         }
       }
-      vnew = bestq >= (kOne >> 1) ? kOne : (bestq << 1);  // Q2.62 -> Q1.63, clamp at 1
+      if (!ok) {
+        // give-up path: let the copies already issued land before the CTA exits
+        for (int s = 0; s < kStages; ++s)
+          if (pending_round[s] >= 0) wait_phase(&S.full[s], pending_round[s] & 1, err, true);
+      }
     }
-    if (lane == 0) {
-      Vout[s] = vnew;
-      if (P.policy_mode == 1)
-        P.policy[(size_t)(P.horizon - k_iter) * P.n_states + s] = best;
-      else if (P.policy_mode == 2)
-        P.policy[s] = best;
-    }
-    if (P.infinite) {
-      const uint64_t vold = Vin[s];
-      const uint64_t d = vnew > vold ? vnew - vold : vold - vnew;
-      run_max = d > run_max ? d : run_max;
+  } else {
+    // ------------------------------------------------------------ consumers
+    WarpScratch* ws = &S.ws[warp];
+    const int ctid = threadIdx.x;  // 0 .. 32*kConsumerWarps-1
+    int i = 0;
+    for (int32_t t = blockIdx.x; t < L.n_tiles; t += gridDim.x, ++i) {
+      const int stage = i % kStages, round = i / kStages;
+      // one thread waits (bounded) and the consumer warps act on its verdict
+      // together, so no warp can be left alone in the named barrier below
+      if (ctid == 0) S.go = wait_phase(&S.full[stage], round & 1, err, false) ? 1 : 0;
+      consumer_sync();
+      if (!S.go) break;
+      (void)mbar_try_wait(&S.full[stage], round & 1);  // completed phase: acquire for this thread
+      const Tile T = L.tiles[t];
+      Stage& st = S.st[stage];
+      if (st.active) {
+        const int32_t k_iter = st.k_iter;
+        unsigned long long dmax = 0;
+        bool infinite;
+        if (!T.big) {
+          const Problem& P = st.prob;
+          const bool pess = P.pessimistic != 0;
+          const uint64_t* __restrict__ Vin = P.V[(k_iter - 1) & 1];
+          uint64_t* __restrict__ Vout = P.V[k_iter & 1];
+          infinite = P.infinite != 0;
+          const int32_t eb = T.e0 & ~3, cb = T.c0 & ~3, mb = T.c0 & ~1, sb = T.s0 & ~3;
+          for (int32_t c = T.c0 + warp; c < T.c1; c += kConsumerWarps) {
+            const int32_t ca = st.cptr[c - cb], ce = st.cptr[c + 1 - cb];
+            const uint64_t q = column_q(st.rows + (ca - eb), st.lg + (ca - T.e0), st.keys + (ca - T.e0), ce - ca,
+                                        st.rem[c - mb], Vin, pess, ws, lane);
+            if (lane == 0) st.q[c - T.c0] = q;
+          }
+          consumer_sync();
+          // opt over each state's actions, mask, policy, residual (thread per state)
+          for (int32_t s = T.s0 + ctid; s < T.s1; s += 32 * kConsumerWarps) {
+            const uint8_t fx = st.fixed[st.fixed_off + (s - T.s0)];
+            uint64_t vnew;
+            int32_t best = -1;
+            if (fx == 1) {
+              vnew = kOne;
+            } else if (fx == 2) {
+              vnew = 0;
+            } else {
+              const int32_t jb = st.sptr[s - sb], je = st.sptr[s + 1 - sb];
+              uint64_t bestq = 0;
+              for (int32_t j = jb; j < je; ++j) {
+                const uint64_t q = st.q[j - T.c0];
+                if (best < 0 || (P.maximize ? q > bestq : q < bestq)) {
+                  bestq = q;
+                  best = j - jb;
+                }
+              }
+              vnew = bestq >= (kOne >> 1) ? kOne : (bestq << 1);  // Q2.62 -> Q1.63, clamp at 1
+            }
+            finish_state(P, s, k_iter, vnew, best, Vin, Vout, dmax);
+          }
+        } else {
+          // one state too large for a stage: warp 0 reads its columns from global memory
+          const Problem& P = L.probs[T.p];
+          infinite = P.infinite != 0;
+          if (warp == 0) {
+            const bool pess = P.pessimistic != 0;
+            const uint64_t* __restrict__ Vin = P.V[(k_iter - 1) & 1];
+            uint64_t* __restrict__ Vout = P.V[k_iter & 1];
+            const int32_t s = T.s0;
+            const uint8_t fx = P.fixed[s];
+            uint64_t vnew;
+            int32_t best = -1;
+            if (fx == 1) {
+              vnew = kOne;
+            } else if (fx == 2) {
+              vnew = 0;
+            } else {
+              uint64_t bestq = 0;
+              for (int32_t c = T.c0; c < T.c1; ++c) {
+                const int32_t ca = __ldg(P.colptr + c), ce = __ldg(P.colptr + c + 1);
+                const uint64_t q = column_q(P.rowval + ca, P.lg + ca, nullptr, ce - ca, __ldg(P.rem + c), Vin, pess,
+                                            ws, lane);
+                if (best < 0 || (P.maximize ? q > bestq : q < bestq)) {
+                  bestq = q;
+                  best = c - T.c0;
+                }
+              }
+              vnew = bestq >= (kOne >> 1) ? kOne : (bestq << 1);
+            }
+            if (lane == 0) finish_state(P, s, k_iter, vnew, best, Vin, Vout, dmax);
+          }
+        }
+        if (infinite) {
+          const uint64_t m = warp_max_u64(dmax);
+          if (lane == 0 && m) atomicMax(&L.its[T.p].resmax, (unsigned long long)m);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.empty[stage]);
     }
   }
-  if (cur_p >= 0 && run_max && lane == 0 && L.probs[cur_p].infinite) atomicMax(&L.its[cur_p].resmax, run_max);
 
-  // The last block to finish advances every running problem's iteration state.
+  // The last CTA to finish advances every running problem's iteration state.
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    unsigned int prev = atomicAdd(&L.ctl->finished, 1u);
-    is_last = (prev == gridDim.x - 1);
+    const unsigned int prev = atomicAdd(&L.ctl->finished, 1u);
+    S.is_last = (prev == gridDim.x - 1);
   }
   __syncthreads();
-  if (!is_last) return;
+  if (!S.is_last) return;
   __threadfence();
-  for (int p = threadIdx.x; p < L.count; p += blockDim.x) {
-    IterState* it = &L.its[p];
-    const Problem& P = L.probs[p];
+  for (int q = threadIdx.x; q < L.count; q += blockDim.x) {
+    IterState* it = &L.its[q];
+    const Problem& PQ = L.probs[q];
     if (it->done) continue;
-    const int32_t k_iter = it->iter + 1;
-    if (!P.infinite && k_iter > P.horizon) {  // horizon 0: nothing ran
+    const int32_t kq = it->iter + 1;
+    if (!PQ.infinite && kq > PQ.horizon) {  // horizon 0: nothing ran
       it->done = 1;
       it->k_final = it->iter;
       continue;
     }
-    it->iter = k_iter;
-    if (P.infinite) {
+    it->iter = kq;
+    if (PQ.infinite) {
       const unsigned long long r = it->resmax;
       it->resmax = 0;
-      if (r < P.eps_fix) {
+      if (r < PQ.eps_fix) {
         it->done = 1;
-        it->k_final = k_iter;
-      } else if (k_iter >= P.horizon) {
+        it->k_final = kq;
+      } else if (kq >= PQ.horizon) {
         it->done = 1;
-        it->k_final = k_iter;
+        it->k_final = kq;
         it->noconv = 1;
       }
-    } else if (k_iter >= P.horizon) {
+    } else if (kq >= PQ.horizon) {
       it->done = 1;
-      it->k_final = k_iter;
+      it->k_final = kq;
     }
   }
   if (threadIdx.x == 0) L.ctl->finished = 0;
@@ -363,32 +562,56 @@ __global__ void __launch_bounds__(kThreads) bellman_step_kernel(StepLaunch L) {
 
 }  // namespace
 
-int choose_col_class(int32_t max_col) {
-  if (max_col <= 32) return 1;
-  if (max_col <= 64) return 2;
-  if (max_col <= 128) return 4;
-  if (max_col <= 256) return 8;
-  return 16;
+void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out) {
+  const std::vector<int32_t>& sp = m->h_stateptr;
+  const std::vector<int32_t>& cp = m->h_colptr;
+  const int32_t n = m->n_states;
+  int32_t s = 0;
+  while (s < n) {
+    Tile T;
+    T.p = problem;
+    T.s0 = s;
+    T.c0 = sp[s];
+    T.e0 = cp[sp[s]];
+    const int32_t ent = cp[sp[s + 1]] - T.e0;
+    if (ent > kTileEntries || sp[s + 1] - sp[s] > kTileCols) {
+      T.s1 = s + 1;
+      T.big = 1;
+    } else {
+      int32_t t = s + 1;
+      while (t < n && cp[sp[t + 1]] - T.e0 <= kTileEntries && sp[t + 1] - T.c0 <= kTileCols &&
+             t + 1 - s <= kTileStates)
+        ++t;
+      T.s1 = t;
+      T.big = 0;
+    }
+    T.c1 = sp[T.s1];
+    T.e1 = cp[T.c1];
+    out.push_back(T);
+    s = T.s1;
+  }
 }
 
-int bellman_grid(int total_states, int col_class) {
+int choose_col_class(int32_t) { return 1; }
+
+int bellman_grid(int, int) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = col_class >= 16 ? 2 : (col_class >= 8 ? 3 : 4);
-  const int want = (total_states + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  const int cap = sms * per_sm * 8;  // a few waves of resident blocks
-  return want < cap ? (want > 0 ? want : 1) : cap;
+  return sms;  // persistent: one CTA per SM
 }
 
 cudaError_t launch_bellman_step(const StepLaunch& L, int grid, cudaStream_t st) {
-  switch (L.col_class) {
-    case 1: bellman_step_kernel<1><<<grid, kThreads, 0, st>>>(L); break;
-    case 2: bellman_step_kernel<2><<<grid, kThreads, 0, st>>>(L); break;
-    case 4: bellman_step_kernel<4><<<grid, kThreads, 0, st>>>(L); break;
-    case 8: bellman_step_kernel<8><<<grid, kThreads, 0, st>>>(L); break;
-    default: bellman_step_kernel<16><<<grid, kThreads, 0, st>>>(L); break;
+  static int configured[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !configured[dev]) {
+    const cudaError_t e = cudaFuncSetAttribute(bellman_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sizeof(Smem));
+    if (e != cudaSuccess) return e;
+    configured[dev] = 1;
   }
+  bellman_step_kernel<<<grid, kBlockThreads, sizeof(Smem), st>>>(L);
   return cudaGetLastError();
 }
 

@@ -31,6 +31,21 @@ constexpr int kThreads = 32 * kWarpsPerBlock;
 // Property kinds inside the kernels.
 enum : int32_t { kPropReach = 0, kPropReachAvoid = 1, kPropReward = 2 };
 
+// A tile is a run of consecutive states of one problem whose entries are
+// streamed into shared memory by one bulk copy per array (state-aligned, so a
+// CTA finishes the opt over actions on its own). A state with more than
+// kTileEntries entries forms a tile of its own that is read from global memory.
+constexpr int kTileEntries = 3584;  // entries per tile (rowval 14 KB + bounds 56 KB + keys 28 KB)
+constexpr int kTileCols = 256;      // columns per tile
+constexpr int kTileStates = 256;    // states per tile
+struct Tile {
+  int32_t p;      // problem
+  int32_t s0, s1; // states [s0, s1) of that problem
+  int32_t c0, c1; // columns [c0, c1)
+  int32_t e0, e1; // entries [e0, e1)
+  int32_t big;    // 1: entries exceed a stage, consumers read global memory
+};
+
 // Device-resident model (the "IntervalMDP.cu(problem)" transfer of Sec. 3.2,
 // CSC layout of Sec. 3.1 / Appendix A).
 struct DevModel {
@@ -45,10 +60,17 @@ struct DevModel {
   ulonglong2* lg = nullptr;     // nnz x {lower, gap = upper - lower} in Q1.63
   uint64_t* rem = nullptr;      // n_cols: 1 - sum(lower) in Q1.63 (clamped at 0)
   size_t bytes = 0;
+  std::vector<int32_t> h_stateptr;  // host copies of the structure (tile planning)
+  std::vector<int32_t> h_colptr;
+  std::vector<Tile> h_tiles;        // tile plan of this model (problem index 0)
+  Tile* tiles = nullptr;            // device copy of h_tiles
+  int32_t n_tiles = 0;
 };
 
+
+
 // One problem of a batch as the step kernel sees it (read-only during a launch).
-struct Problem {
+struct alignas(16) Problem {
   const int32_t* stateptr;
   const int32_t* colptr;
   const int32_t* rowval;
@@ -81,7 +103,7 @@ struct IterState {
 
 struct StepControl {
   unsigned int finished;  // blocks finished in the running launch
-  unsigned int pad;
+  unsigned int error;     // nonzero: a bounded wait inside the kernel gave up
 };
 
 struct StepLaunch {
@@ -92,13 +114,18 @@ struct StepLaunch {
   int32_t count;
   int32_t total_states;
   int32_t any_infinite;
-  int32_t col_class;  // register class E of the column routine
+  int32_t col_class;  // unused by the tiled kernel (kept for the launch helpers)
+  const Tile* tiles;
+  int32_t n_tiles;
+  int32_t _pad2;
 };
 
 // bellman.cu
 cudaError_t launch_bellman_step(const StepLaunch& L, int grid, cudaStream_t st);
 int choose_col_class(int32_t max_col);
 int bellman_grid(int total_states, int col_class);
+// Tile plan for one problem's model (host), appended to `out`.
+void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out);
 
 // model.cu
 imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, const int32_t* stateptr,
@@ -107,6 +134,12 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
 void model_destroy(DevModel* m);
 
 // session.cu: resident device state of value iteration for a batch of problems.
+// Padding of the per-state / per-column arrays so that 16-byte-aligned bulk-copy
+// windows around any index range stay inside their allocations.
+inline size_t padded_i32(size_t n) { return ((n + 3) & ~size_t(3)) + 4; }
+inline size_t padded_u64(size_t n) { return ((n + 1) & ~size_t(1)) + 2; }
+inline size_t padded_u8(size_t n) { return ((n + 15) & ~size_t(15)) + 16; }
+
 struct Session {
   int device = 0;
   int count = 0;
@@ -123,6 +156,8 @@ struct Session {
   Problem* probs = nullptr;
   IterState* its = nullptr;
   StepControl* ctl = nullptr;
+  Tile* tiles = nullptr;
+  int32_t n_tiles = 0;
   StepLaunch L{};
   int grid = 1;
   cudaGraphExec_t graph = nullptr;

@@ -83,6 +83,7 @@ void model_destroy(DevModel* m) {
   cudaFree(m->rowval);
   cudaFree(m->lg);
   cudaFree(m->rem);
+  cudaFree(m->tiles);
   delete m;
 }
 
@@ -130,18 +131,22 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
   m->max_col = max_col;
   m->dtype = dtype;
   const size_t nz = (size_t)std::max<int64_t>(nnz, 1);
-  const bool ok = cudaMalloc(&m->stateptr, sizeof(int32_t) * (n_states + 1)) == cudaSuccess &&
-                  cudaMalloc(&m->colptr, sizeof(int32_t) * (n_cols + 1)) == cudaSuccess &&
-                  cudaMalloc(&m->rowval, sizeof(int32_t) * nz) == cudaSuccess &&
+  // rowval is padded to a multiple of 4 entries plus 4, so that bulk copies of
+  // 16-byte-aligned windows around any entry range stay inside the allocation.
+  const size_t nz_rows = ((nz + 3) & ~size_t(3)) + 4;
+  const size_t ns_pad = padded_i32(n_states + 1), nc_pad = padded_i32(n_cols + 1), nr_pad = padded_u64(n_cols);
+  const bool ok = cudaMalloc(&m->stateptr, sizeof(int32_t) * ns_pad) == cudaSuccess &&
+                  cudaMalloc(&m->colptr, sizeof(int32_t) * nc_pad) == cudaSuccess &&
+                  cudaMalloc(&m->rowval, sizeof(int32_t) * nz_rows) == cudaSuccess &&
                   cudaMalloc(&m->lg, sizeof(ulonglong2) * nz) == cudaSuccess &&
-                  cudaMalloc(&m->rem, sizeof(uint64_t) * n_cols) == cudaSuccess;
+                  cudaMalloc(&m->rem, sizeof(uint64_t) * nr_pad) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     model_destroy(m);
     set_error("device allocation failed for the model");
     return IMDP_ENOMEM;
   }
-  m->bytes = sizeof(int32_t) * (n_states + 1 + n_cols + 1 + nz) + sizeof(ulonglong2) * nz + sizeof(uint64_t) * n_cols;
+  m->bytes = sizeof(int32_t) * (ns_pad + nc_pad + nz_rows) + sizeof(ulonglong2) * nz + sizeof(uint64_t) * nr_pad;
 
   // Bounds: device pointers are used in place, host arrays are staged.
   DevBuf dlo, dup, derr;
@@ -157,8 +162,12 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
   }
   if (cudaMalloc(&derr.p, sizeof(unsigned)) != cudaSuccess) { cudaGetLastError(); model_destroy(m); set_error("allocation failed"); return IMDP_ENOMEM; }
 
-  e = cudaMemcpyAsync(m->stateptr, hs.data(), sizeof(int32_t) * hs.size(), cudaMemcpyHostToDevice, st);
+  e = cudaMemsetAsync(m->stateptr, 0, sizeof(int32_t) * ns_pad, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->colptr, 0, sizeof(int32_t) * nc_pad, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->rem, 0, sizeof(uint64_t) * nr_pad, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->stateptr, hs.data(), sizeof(int32_t) * hs.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(m->colptr, hc.data(), sizeof(int32_t) * hc.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->rowval + nnz, 0, sizeof(int32_t) * (nz_rows - nnz), st);
   if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(m->rowval, rowval, sizeof(int32_t) * nnz, cudaMemcpyDefault, st);
   if (e == cudaSuccess && lo_d != lower) e = cudaMemcpyAsync((void*)lo_d, lower, sizeof(double) * nnz, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && up_d != upper) e = cudaMemcpyAsync((void*)up_d, upper, sizeof(double) * nnz, cudaMemcpyHostToDevice, st);
@@ -188,6 +197,20 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
     set_error("infeasible column: need 0 <= lower <= upper <= 1 and sum lower <= 1 <= sum upper (tol 1e-12)");
     return IMDP_EINFEASIBLE;
   }
+  m->h_stateptr = std::move(hs);
+  m->h_colptr = std::move(hc);
+  plan_tiles(m, 0, m->h_tiles);
+  m->n_tiles = (int32_t)m->h_tiles.size();
+  if (cudaMalloc(&m->tiles, sizeof(Tile) * m->h_tiles.size()) != cudaSuccess) {
+    cudaGetLastError();
+    model_destroy(m);
+    set_error("device allocation failed for the tile plan");
+    return IMDP_ENOMEM;
+  }
+  m->bytes += sizeof(Tile) * m->h_tiles.size();
+  e = cudaMemcpyAsync(m->tiles, m->h_tiles.data(), sizeof(Tile) * m->h_tiles.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { model_destroy(m); return cuda_status(e, "upload tile plan"); }
   *out = m;
   return IMDP_OK;
 }

@@ -186,6 +186,8 @@ extern "C" IMDP_API imdp_status imdp_value_iteration_noalloc(imdp_model* m, cons
   L.total_states = n;
   L.any_infinite = P.infinite;
   L.col_class = choose_col_class(dm->max_col);
+  L.tiles = dm->tiles;  // the model's own tile plan (problem index 0)
+  L.n_tiles = dm->n_tiles;
   const int grid = bellman_grid(n, L.col_class);
   IterState hs;
   std::memset(&hs, 0, sizeof(hs));
@@ -210,6 +212,15 @@ extern "C" IMDP_API imdp_status imdp_value_iteration_noalloc(imdp_model* m, cons
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, d_it, sizeof(hs), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e, "noalloc export");
+  StepControl hc;
+  std::memset(&hc, 0, sizeof(hc));
+  e = cudaMemcpyAsync(&hc, d_ctl, sizeof(hc), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "noalloc status");
+  if (hc.error) {
+    set_error("a bounded wait inside the Bellman kernel gave up");
+    return IMDP_ETIMEOUT;
+  }
   if (k_out) *k_out = hs.done ? hs.k_final : hs.iter;
   if (hs.noconv) {
     set_error("infinite horizon did not converge within the iteration cap");

@@ -119,13 +119,21 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
       }
     max_class = std::max(max_class, choose_col_class(ms[p]->max_col));
   }
-  S->fixed = S->alloc<uint8_t>(total);
+  std::vector<Tile> tiles;
+  for (int p = 0; p < count; ++p) {
+    const size_t at = tiles.size();
+    tiles.insert(tiles.end(), ms[p]->h_tiles.begin(), ms[p]->h_tiles.end());
+    for (size_t t = at; t < tiles.size(); ++t) tiles[t].p = p;
+  }
+  S->n_tiles = (int32_t)tiles.size();
+  S->tiles = S->alloc<Tile>(tiles.size());
+  S->fixed = S->alloc<uint8_t>(padded_u8(total));
   S->V = S->alloc<uint64_t>(2 * total);
   S->base = S->alloc<int32_t>(count + 1);
   S->probs = S->alloc<Problem>(count);
   S->its = S->alloc<IterState>(count);
   S->ctl = S->alloc<StepControl>(1);
-  if (!S->fixed || !S->V || !S->base || !S->probs || !S->its || !S->ctl) {
+  if (!S->tiles || !S->fixed || !S->V || !S->base || !S->probs || !S->its || !S->ctl) {
     delete S; set_error("device allocation failed (session)"); return IMDP_ENOMEM;
   }
   S->probs_h.resize(count);
@@ -160,9 +168,11 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
       S->policy_cells[p] = (int64_t)cells;
     }
   }
-  cudaError_t e = cudaMemcpyAsync(S->fixed, fixed.data(), total, cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemsetAsync(S->fixed, 0, padded_u8(total), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->fixed, fixed.data(), total, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S->base, S->base_h.data(), sizeof(int32_t) * (count + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S->probs, S->probs_h.data(), sizeof(Problem) * count, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host staging vectors go out of scope
   if (e != cudaSuccess) { delete S; return cuda_status(e, "session setup"); }
   S->L.probs = S->probs;
@@ -173,6 +183,8 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   S->L.total_states = (int32_t)total;
   S->L.any_infinite = S->any_infinite ? 1 : 0;
   S->L.col_class = max_class;
+  S->L.tiles = S->tiles;
+  S->L.n_tiles = S->n_tiles;
   S->grid = bellman_grid((int)total, max_class);
   imdp_status r = S->reset(st);
   if (r != IMDP_OK) { delete S; return r; }
@@ -225,9 +237,15 @@ imdp_status Session::step(int32_t n, cudaStream_t st) {
 
 imdp_status Session::read_states(std::vector<IterState>& out, cudaStream_t st) {
   out.resize(count);
+  StepControl c{};
   cudaError_t e = cudaMemcpyAsync(out.data(), its, sizeof(IterState) * count, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&c, ctl, sizeof(StepControl), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e, "read iteration state");
+  if (c.error) {
+    set_error("a bounded wait inside the Bellman kernel gave up (results of this session are invalid)");
+    return IMDP_ETIMEOUT;
+  }
   return IMDP_OK;
 }
 
