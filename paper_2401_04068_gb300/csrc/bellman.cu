@@ -49,7 +49,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBins = 64;
-constexpr int kConsumerWarps = 8;
+constexpr int kConsumerWarps = 12;
 constexpr int kStages = 2;
 constexpr int kBlockThreads = 32 * (kConsumerWarps + 1);
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz: bound of every wait
@@ -58,7 +58,6 @@ struct WarpScratch {
   unsigned int hl[kBins];        // gap sum per bin, low 32 bits (wraps)
   unsigned int hh[kBins];        // gap sum per bin, high 32 bits plus the low part's carries
   unsigned int hc[kBins];        // entry count per bin
-  unsigned int _pad[kBins];
   unsigned long long ck[32];     // compacted candidates: key
   unsigned long long cg[32];     //                       gap
 };
@@ -78,7 +77,7 @@ struct Stage {
   int32_t active;                        // set by the producer: the problem still runs
   int32_t k_iter;                        //                      iteration being computed
   int32_t fixed_off;                     //                      offset of state s0 in `fixed`
-  int32_t _pad;
+  unsigned int done;                     // column slots of this tile finished so far
 };
 
 struct Smem {
@@ -87,7 +86,6 @@ struct Smem {
   unsigned long long full[kStages];
   unsigned long long empty[kStages];
   int is_last;
-  volatile int go;
 };
 static_assert(sizeof(int32_t) * (kTileEntries + 8) % 16 == 0, "lg must stay 16-byte aligned");
 static_assert(offsetof(Stage, rem) % 16 == 0 && offsetof(Stage, sptr) % 16 == 0 && offsetof(Stage, cptr) % 16 == 0 &&
@@ -125,9 +123,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
-}
-__device__ __forceinline__ void consumer_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(32 * kConsumerWarps) : "memory");
 }
 
 // Wait for phase `parity` of an mbarrier, giving up after kWaitCycles or when
@@ -363,6 +358,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
+      S.st[s].done = 0;  // shared memory starts undefined in every launch
       mbar_init(&S.full[s], 1);
       mbar_init(&S.empty[s], kConsumerWarps);
     }
@@ -424,99 +420,120 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
     }
   } else {
     // ------------------------------------------------------------ consumers
+    // The CTA's tiles t_j = blockIdx.x + j*gridDim.x are visited in order by
+    // every consumer warp: wait until tile j has landed, work on its own slots,
+    // arrive on the stage's "empty" barrier. Slots (one per column; one for a
+    // tile read from global memory) are dealt round-robin across tiles, so a
+    // warp that has no column left in tile j moves on to tile j+1 while the
+    // others finish. Because every warp visits every tile, no warp can fall two
+    // rounds behind a stage, which keeps the parity waits unambiguous. The warp
+    // that completes a tile's last slot runs the tile's state epilogue before it
+    // arrives, so the producer refills a stage only after the epilogue.
     WarpScratch* ws = &S.ws[warp];
-    const int ctid = threadIdx.x;  // 0 .. 32*kConsumerWarps-1
-    int i = 0;
-    for (int32_t t = blockIdx.x; t < L.n_tiles; t += gridDim.x, ++i) {
-      const int stage = i % kStages, round = i / kStages;
-      // one thread waits (bounded) and the consumer warps act on its verdict
-      // together, so no warp can be left alone in the named barrier below
-      if (ctid == 0) S.go = wait_phase(&S.full[stage], round & 1, err, false) ? 1 : 0;
-      consumer_sync();
-      if (!S.go) break;
-      (void)mbar_try_wait(&S.full[stage], round & 1);  // completed phase: acquire for this thread
+    int32_t slot_base = 0;  // global slot index of tile j's first slot
+    int j = 0;
+    for (int32_t t = blockIdx.x; t < L.n_tiles; t += gridDim.x, ++j) {
+      const int stage = j % kStages, round = j / kStages;
+      int got = 1;
+      if (lane == 0) got = wait_phase(&S.full[stage], round & 1, err, false) ? 1 : 0;
+      got = __shfl_sync(kFull, got, 0);
+      if (!got) break;
+      (void)mbar_try_wait(&S.full[stage], round & 1);  // completed phase: acquire for every lane
       const Tile T = L.tiles[t];
       Stage& st = S.st[stage];
-      if (st.active) {
-        const int32_t k_iter = st.k_iter;
-        unsigned long long dmax = 0;
-        bool infinite;
-        if (!T.big) {
-          const Problem& P = st.prob;
-          const bool pess = P.pessimistic != 0;
-          const uint64_t* __restrict__ Vin = P.V[(k_iter - 1) & 1];
-          uint64_t* __restrict__ Vout = P.V[k_iter & 1];
-          infinite = P.infinite != 0;
-          const int32_t eb = T.e0 & ~3, cb = T.c0 & ~3, mb = T.c0 & ~1, sb = T.s0 & ~3;
-          for (int32_t c = T.c0 + warp; c < T.c1; c += kConsumerWarps) {
+      const int32_t nslots = T.big ? 1 : T.c1 - T.c0;
+      const int32_t k_iter = st.k_iter;
+      const bool active = st.active != 0;
+      // first local slot of this warp: global slot g with g % kConsumerWarps == warp
+      int32_t first = warp - (slot_base % kConsumerWarps);
+      if (first < 0) first += kConsumerWarps;
+      for (int32_t ls = first; ls < nslots; ls += kConsumerWarps) {
+        if (active) {
+          if (!T.big) {
+            const Problem& P = st.prob;
+            const int32_t c = T.c0 + ls;
+            const int32_t eb = T.e0 & ~3, cb = T.c0 & ~3, mb = T.c0 & ~1;
             const int32_t ca = st.cptr[c - cb], ce = st.cptr[c + 1 - cb];
             const uint64_t q = column_q(st.rows + (ca - eb), st.lg + (ca - T.e0), st.keys + (ca - T.e0), ce - ca,
-                                        st.rem[c - mb], Vin, pess, ws, lane);
-            if (lane == 0) st.q[c - T.c0] = q;
-          }
-          consumer_sync();
-          // opt over each state's actions, mask, policy, residual (thread per state)
-          for (int32_t s = T.s0 + ctid; s < T.s1; s += 32 * kConsumerWarps) {
-            const uint8_t fx = st.fixed[st.fixed_off + (s - T.s0)];
-            uint64_t vnew;
-            int32_t best = -1;
-            if (fx == 1) {
-              vnew = kOne;
-            } else if (fx == 2) {
-              vnew = 0;
-            } else {
-              const int32_t jb = st.sptr[s - sb], je = st.sptr[s + 1 - sb];
-              uint64_t bestq = 0;
-              for (int32_t j = jb; j < je; ++j) {
-                const uint64_t q = st.q[j - T.c0];
-                if (best < 0 || (P.maximize ? q > bestq : q < bestq)) {
-                  bestq = q;
-                  best = j - jb;
-                }
-              }
-              vnew = bestq >= (kOne >> 1) ? kOne : (bestq << 1);  // Q2.62 -> Q1.63, clamp at 1
-            }
-            finish_state(P, s, k_iter, vnew, best, Vin, Vout, dmax);
-          }
-        } else {
-          // one state too large for a stage: warp 0 reads its columns from global memory
-          const Problem& P = L.probs[T.p];
-          infinite = P.infinite != 0;
-          if (warp == 0) {
+                                        st.rem[c - mb], P.V[(k_iter - 1) & 1], P.pessimistic != 0, ws, lane);
+            if (lane == 0) st.q[ls] = q;
+          } else {
+            // one state too large for a stage: this warp reads its columns from global memory
+            const Problem& P = L.probs[T.p];
             const bool pess = P.pessimistic != 0;
             const uint64_t* __restrict__ Vin = P.V[(k_iter - 1) & 1];
-            uint64_t* __restrict__ Vout = P.V[k_iter & 1];
-            const int32_t s = T.s0;
-            const uint8_t fx = P.fixed[s];
-            uint64_t vnew;
+            uint64_t bestq = 0;
             int32_t best = -1;
-            if (fx == 1) {
-              vnew = kOne;
-            } else if (fx == 2) {
-              vnew = 0;
-            } else {
-              uint64_t bestq = 0;
-              for (int32_t c = T.c0; c < T.c1; ++c) {
-                const int32_t ca = __ldg(P.colptr + c), ce = __ldg(P.colptr + c + 1);
-                const uint64_t q = column_q(P.rowval + ca, P.lg + ca, nullptr, ce - ca, __ldg(P.rem + c), Vin, pess,
-                                            ws, lane);
-                if (best < 0 || (P.maximize ? q > bestq : q < bestq)) {
-                  bestq = q;
-                  best = c - T.c0;
-                }
+            for (int32_t cc = T.c0; cc < T.c1; ++cc) {
+              const int32_t ca = __ldg(P.colptr + cc), ce = __ldg(P.colptr + cc + 1);
+              const uint64_t q = column_q(P.rowval + ca, P.lg + ca, nullptr, ce - ca, __ldg(P.rem + cc), Vin, pess,
+                                          ws, lane);
+              if (best < 0 || (P.maximize ? q > bestq : q < bestq)) {
+                bestq = q;
+                best = cc - T.c0;
               }
-              vnew = bestq >= (kOne >> 1) ? kOne : (bestq << 1);
             }
-            if (lane == 0) finish_state(P, s, k_iter, vnew, best, Vin, Vout, dmax);
+            if (lane == 0) {
+              st.q[0] = bestq;
+              st.q[1] = (unsigned long long)(long long)best;
+            }
           }
         }
-        if (infinite) {
-          const uint64_t m = warp_max_u64(dmax);
-          if (lane == 0 && m) atomicMax(&L.its[T.p].resmax, (unsigned long long)m);
+        // count the slot; the warp that completes the tile finishes its states
+        unsigned prev = 0;
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence_block();
+          prev = atomicAdd(&st.done, 1u);
+        }
+        prev = __shfl_sync(kFull, prev, 0);
+        if (prev + 1 == (unsigned)nslots) {
+          __threadfence_block();
+          if (active) {
+            const Problem& P = T.big ? L.probs[T.p] : st.prob;
+            const uint64_t* __restrict__ Vin = P.V[(k_iter - 1) & 1];
+            uint64_t* __restrict__ Vout = P.V[k_iter & 1];
+            unsigned long long dmax = 0;
+            const int32_t sb = T.s0 & ~3;
+            for (int32_t s = T.s0 + lane; s < T.s1; s += 32) {
+              const uint8_t fx = T.big ? P.fixed[s] : st.fixed[st.fixed_off + (s - T.s0)];
+              uint64_t vnew;
+              int32_t best = -1;
+              if (fx == 1) {
+                vnew = kOne;
+              } else if (fx == 2) {
+                vnew = 0;
+              } else {
+                uint64_t bestq = 0;
+                if (T.big) {
+                  bestq = st.q[0];
+                  best = (int32_t)(long long)st.q[1];
+                } else {
+                  const int32_t jb = st.sptr[s - sb], je = st.sptr[s + 1 - sb];
+                  for (int32_t jj = jb; jj < je; ++jj) {
+                    const uint64_t q = st.q[jj - T.c0];
+                    if (best < 0 || (P.maximize ? q > bestq : q < bestq)) {
+                      bestq = q;
+                      best = jj - jb;
+                    }
+                  }
+                }
+                vnew = bestq >= (kOne >> 1) ? kOne : (bestq << 1);  // Q2.62 -> Q1.63, clamp at 1
+              }
+              finish_state(P, s, k_iter, vnew, best, Vin, Vout, dmax);
+            }
+            if (P.infinite) {
+              const uint64_t m = warp_max_u64(dmax);
+              if (lane == 0 && m) atomicMax(&L.its[T.p].resmax, (unsigned long long)m);
+            }
+          }
+          __syncwarp();
+          if (lane == 0) st.done = 0;
         }
       }
+      slot_base += nslots;
       __syncwarp();
-      if (lane == 0) mbar_arrive(&S.empty[stage]);
+      if (lane == 0) mbar_arrive(&S.empty[stage]);  // this warp is done with tile j
     }
   }
 

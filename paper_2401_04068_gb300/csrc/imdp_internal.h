@@ -35,7 +35,7 @@ enum : int32_t { kPropReach = 0, kPropReachAvoid = 1, kPropReward = 2 };
 // streamed into shared memory by one bulk copy per array (state-aligned, so a
 // CTA finishes the opt over actions on its own). A state with more than
 // kTileEntries entries forms a tile of its own that is read from global memory.
-constexpr int kTileEntries = 3584;  // entries per tile (rowval 14 KB + bounds 56 KB + keys 28 KB)
+constexpr int kTileEntries = 3072;  // entries per tile (rowval 12 KB + bounds 48 KB + keys 24 KB)
 constexpr int kTileCols = 256;      // columns per tile
 constexpr int kTileStates = 256;    // states per tile
 struct Tile {
