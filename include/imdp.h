@@ -15,7 +15,9 @@
  *
  * Computation (Eq. 2 / Eq. 3): robust value iteration
  *   V_0 = 1_G,  V_k(s) = 1_G(s) + 1_{S\G}(s) opt^pi_a opt^eta_{p in Gamma_{s,a}} sum_s' V_{k-1}(s') p(s'),
- * with the inner problem solved by O-maximization (Sec. 4).
+ * with the inner problem solved by O-maximization (Sec. 4). The discounted-reward
+ * property (Sec. 3.2, whose recursion the paper leaves to the reader) is taken as
+ *   V_0 = r,  V_k(s) = r(s) + gamma opt^pi_a opt^eta_p sum_s' V_{k-1}(s') p(s').
  *
  * Conventions for every entry point:
  *   - Errors are returned as imdp_status; nothing is thrown across the ABI.

@@ -58,6 +58,8 @@ struct WarpScratch {
   unsigned int hl[kBins];        // gap sum per bin, low 32 bits (wraps)
   unsigned int hh[kBins];        // gap sum per bin, high 32 bits plus the low part's carries
   unsigned int hc[kBins];        // entry count per bin
+  unsigned int hsat[2];          // bins whose sum passed 2^64 (saturated)
+  int ci[32];                    // compacted candidates: entry index
   unsigned long long ck[32];     // compacted candidates: key
   unsigned long long cg[32];     //                       gap
 };
@@ -159,120 +161,193 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
   const unsigned c = __reduce_add_sync(kFull, (unsigned)(x >> 44));
   return (uint64_t)a + ((uint64_t)b << 22) + ((uint64_t)c << 44);
 }
-__device__ __forceinline__ uint64_t warp_excl_scan_u64(uint64_t x, int lane) {
+
+// ---------------------------------------------------------------- saturating sums
+//
+// Gap sums decide only whether a prefix reaches rem (<= 2^63), and any sum that
+// is below rem is needed exactly. So every gap enters the sums clipped to rem
+// (which changes no decision: a gap >= rem reaches rem on its own), and sums
+// saturate at 2^64 - 1 instead of wrapping (a column's upper bounds may add up
+// to far more than 1).
+
+__device__ __forceinline__ uint64_t sat_add(uint64_t a, uint64_t b) {
+  const uint64_t c = a + b;
+  return c < a ? ~0ull : c;
+}
+// Warp sum of per-lane values <= 2^63, saturating at 2^64 - 1.
+__device__ __forceinline__ uint64_t warp_sum_sat(uint64_t x) {
+  x = x > kOne ? kOne : x;
+  const unsigned a = __reduce_add_sync(kFull, (unsigned)(x & 0x3fffffu));
+  const unsigned b = __reduce_add_sync(kFull, (unsigned)((x >> 22) & 0x1fffffu));
+  const unsigned c = __reduce_add_sync(kFull, (unsigned)(x >> 43));
+  const unsigned __int128 t = (unsigned __int128)a + ((unsigned __int128)b << 22) + ((unsigned __int128)c << 43);
+  return (t >> 64) ? ~0ull : (uint64_t)t;
+}
+__device__ __forceinline__ uint64_t warp_excl_scan_sat(uint64_t x, int lane) {
   uint64_t incl = x;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint64_t y = __shfl_up_sync(kFull, incl, o);
-    if (lane >= o) incl += y;
+    if (lane >= o) incl = sat_add(incl, y);
   }
-  return incl - x;
+  // exclusive = inclusive of the previous lane
+  const uint64_t ex = __shfl_up_sync(kFull, incl, 1);
+  return lane == 0 ? 0ull : ex;
 }
 
 // ---------------------------------------------------------------- one column
 
 // Entries [0, k) of one column: destinations `rows`, bound pairs `lg`, key
 // scratch `keys` (shared memory; nullptr = recompute keys from V on every pass,
-// used when the column is read straight from global memory). Returns q in Q2.62.
+// used when the column is read straight from global memory). `hint` is the entry
+// that held the threshold in the previous iteration (-1: none); the entry that
+// holds it now is returned in *hint_out. Returns q in Q2.62.
 __device__ uint64_t column_q(const int32_t* rows, const ulonglong2* lg, unsigned long long* keys, int32_t k,
-                             uint64_t rem, const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane) {
+                             uint64_t rem, const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane,
+                             int32_t hint, int32_t* hint_out) {
   auto key_of = [&](int idx) -> uint64_t {
     if (keys) return keys[idx];
     const uint64_t v = __ldg(V + rows[idx]);
     return pess ? v : (kOne - v);
   };
-  // 1. keys and their range
-  uint64_t lmin = ~0ull, lmax = 0;
+  // 1. keys (stored in shared memory for the later passes)
+  if (keys) {
 #pragma unroll 4
-  for (int idx = lane; idx < k; idx += 32) {
-    const uint64_t v = __ldg(V + rows[idx]);
-    const uint64_t key = pess ? v : (kOne - v);
-    if (keys) keys[idx] = key;
-    lmin = key < lmin ? key : lmin;
-    lmax = key > lmax ? key : lmax;
+    for (int idx = lane; idx < k; idx += 32) {
+      const uint64_t v = __ldg(V + rows[idx]);
+      keys[idx] = pess ? v : (kOne - v);
+    }
+    __syncwarp();
   }
-  __syncwarp();
 
-  // 2. threshold search: after it, keys < lo are below (full gap), keys > hi are
-  // above (lower bound), keys in [lo, hi] are candidates sharing rem - fb.
-  uint64_t lo = 0, hi = 0, fb = 0;
-  bool all_below = false, uniform = true;  // rem == 0: every entry keeps its lower bound
-  if (rem != 0) {
-    uniform = false;
-    uint64_t cmin = warp_min_u64(lmin), cmax = warp_max_u64(lmax);
-    lo = 0;
-    hi = kOne;
-    for (int round = 0; round < 12; ++round) {
-      if (cmin > cmax) {  // no entry: nothing absorbs rem
-        all_below = true;
-        break;
+  if (rem == 0) {  // nothing to hand out: every entry keeps its lower bound
+    uint64_t acc = 0;
+    for (int idx = lane; idx < k; idx += 32) {
+      const uint64_t key = key_of(idx);
+      acc += __umul64hi(pess ? key : (kOne - key), lg[idx].x);
+    }
+    *hint_out = hint;
+    return warp_sum_u64(acc);
+  }
+
+  // 2. warm start: does last iteration's threshold entry still hold it? With
+  // kappa its key, it does exactly when F(< kappa) < rem <= F(<= kappa), F being
+  // the gap sum; then one pass gives q.
+  if (hint >= 0 && hint < k) {
+    const uint64_t kap = key_of(hint);
+    uint64_t acc = 0, flt = 0, geq = 0;
+    for (int idx = lane; idx < k; idx += 32) {
+      const uint64_t key = key_of(idx);
+      const ulonglong2 b = lg[idx];
+      const uint64_t v = pess ? key : (kOne - key);
+      const uint64_t g = b.y < rem ? b.y : rem;
+      if (key < kap) {
+        acc += __umul64hi(v, b.x + b.y);
+        flt = sat_add(flt, g);
+      } else {
+        acc += __umul64hi(v, b.x);
+        if (key == kap) geq = sat_add(geq, g);
       }
-      if (cmin == cmax) {  // the candidates share one key
-        lo = hi = cmin;
-        uniform = true;
-        break;
-      }
-      const int bits = 64 - __clzll((long long)(cmax - cmin));
-      const int shift = bits > 6 ? bits - 6 : 0;
-      ws->hl[lane] = 0;
-      ws->hl[lane + 32] = 0;
-      ws->hh[lane] = 0;
-      ws->hh[lane + 32] = 0;
-      ws->hc[lane] = 0;
-      ws->hc[lane + 32] = 0;
-      __syncwarp();
-      for (int idx = lane; idx < k; idx += 32) {
-        const uint64_t key = key_of(idx);
-        if (key >= lo && key <= hi) {
-          const int b = (int)((key - cmin) >> shift);
-          const uint64_t g = lg[idx].y;
-          // exact 64-bit bin sums from native 32-bit atomics: the adder whose
-          // low-word addition wraps carries one into the high word
-          const unsigned gl = (unsigned)g;
-          const unsigned old = atomicAdd(&ws->hl[b], gl);
-          const unsigned up = (unsigned)(g >> 32) + ((old + gl) < old ? 1u : 0u);
-          if (up) atomicAdd(&ws->hh[b], up);
-          atomicAdd(&ws->hc[b], 1u);
-        }
-      }
-      __syncwarp();
-      const uint64_t h0 = ((uint64_t)ws->hh[2 * lane] << 32) | ws->hl[2 * lane];
-      const uint64_t h1 = ((uint64_t)ws->hh[2 * lane + 1] << 32) | ws->hl[2 * lane + 1];
-      const uint64_t ex = warp_excl_scan_u64(h0 + h1, lane);
-      const uint64_t i0 = fb + ex + h0, i1 = i0 + h1;
-      const unsigned cross = __ballot_sync(kFull, i1 >= rem);
-      if (cross == 0) {  // first round only: the gaps cannot absorb rem
-        all_below = true;
-        break;
-      }
-      const int L = __ffs(cross) - 1;
-      const bool first = i0 >= rem;
-      const int b = __shfl_sync(kFull, first ? 2 * lane : 2 * lane + 1, L);
-      fb = __shfl_sync(kFull, first ? fb + ex : i0, L);
-      const unsigned cnt = ws->hc[b];
-      __syncwarp();
-      lo = cmin + ((uint64_t)b << shift);
-      const uint64_t top = lo + ((1ull << shift) - 1ull);
-      hi = top < cmax ? top : cmax;
-      if (cnt <= 32) break;
-      // narrow to the min/max of the crossing bin's entries
-      uint64_t a = ~0ull, z = 0;
-      for (int idx = lane; idx < k; idx += 32) {
-        const uint64_t key = key_of(idx);
-        if (key >= lo && key <= hi) {
-          a = key < a ? key : a;
-          z = key > z ? key : z;
-        }
-      }
-      cmin = warp_min_u64(a);
-      cmax = warp_max_u64(z);
+    }
+    flt = warp_sum_sat(flt);
+    geq = warp_sum_sat(geq);
+    if (flt < rem && rem - flt <= geq) {
+      *hint_out = hint;
+      return warp_sum_u64(acc) + __umul64hi(pess ? kap : (kOne - kap), rem - flt);
     }
   }
 
-  // 3. final pass: lower bounds everywhere, full gaps below the candidates,
+  // 3. threshold search: after it, keys < lo are below (full gap), keys > hi are
+  // above (lower bound), keys in [lo, hi] are candidates sharing rem - fb.
+  uint64_t lmin = ~0ull, lmax = 0;
+  for (int idx = lane; idx < k; idx += 32) {
+    const uint64_t key = key_of(idx);
+    lmin = key < lmin ? key : lmin;
+    lmax = key > lmax ? key : lmax;
+  }
+  uint64_t lo = 0, hi = kOne, fb = 0;
+  bool all_below = false, uniform = false;
+  uint64_t cmin = warp_min_u64(lmin), cmax = warp_max_u64(lmax);
+  for (int round = 0; round < 12; ++round) {
+    if (cmin > cmax) {  // no entry: nothing absorbs rem
+      all_below = true;
+      break;
+    }
+    if (cmin == cmax) {  // the candidates share one key
+      lo = hi = cmin;
+      uniform = true;
+      break;
+    }
+    const int bits = 64 - __clzll((long long)(cmax - cmin));
+    const int shift = bits > 6 ? bits - 6 : 0;
+    ws->hl[lane] = 0;
+    ws->hl[lane + 32] = 0;
+    ws->hh[lane] = 0;
+    ws->hh[lane + 32] = 0;
+    ws->hc[lane] = 0;
+    ws->hc[lane + 32] = 0;
+    if (lane == 0) ws->hsat[0] = ws->hsat[1] = 0;
+    __syncwarp();
+    for (int idx = lane; idx < k; idx += 32) {
+      const uint64_t key = key_of(idx);
+      if (key >= lo && key <= hi) {
+        const int b = (int)((key - cmin) >> shift);
+        const uint64_t g = lg[idx].y < rem ? lg[idx].y : rem;
+        // exact 64-bit bin sums from native 32-bit atomics: the adder whose
+        // low-word addition wraps carries one into the high word; a wrap of the
+        // high word marks the bin saturated
+        const unsigned gl = (unsigned)g;
+        const unsigned old = atomicAdd(&ws->hl[b], gl);
+        const unsigned up = (unsigned)(g >> 32) + ((old + gl) < old ? 1u : 0u);
+        if (up) {
+          const unsigned oh = atomicAdd(&ws->hh[b], up);
+          if (oh + up < oh) atomicOr(&ws->hsat[b >> 5], 1u << (b & 31));
+        }
+        atomicAdd(&ws->hc[b], 1u);
+      }
+    }
+    __syncwarp();
+    const unsigned sat = ws->hsat[lane >> 4];
+    const uint64_t h0 = ((sat >> ((2 * lane) & 31)) & 1u) ? ~0ull
+                                                          : (((uint64_t)ws->hh[2 * lane] << 32) | ws->hl[2 * lane]);
+    const uint64_t h1 = ((sat >> ((2 * lane + 1) & 31)) & 1u)
+                            ? ~0ull
+                            : (((uint64_t)ws->hh[2 * lane + 1] << 32) | ws->hl[2 * lane + 1]);
+    const uint64_t ex = warp_excl_scan_sat(sat_add(h0, h1), lane);
+    const uint64_t i0 = sat_add(sat_add(fb, ex), h0), i1 = sat_add(i0, h1);
+    const unsigned cross = __ballot_sync(kFull, i1 >= rem);
+    if (cross == 0) {  // first round only: the gaps cannot absorb rem
+      all_below = true;
+      break;
+    }
+    const int L = __ffs(cross) - 1;
+    const bool first = i0 >= rem;
+    const int b = __shfl_sync(kFull, first ? 2 * lane : 2 * lane + 1, L);
+    fb = __shfl_sync(kFull, first ? sat_add(fb, ex) : i0, L);  // < rem by the choice of b
+    const unsigned cnt = ws->hc[b];
+    __syncwarp();
+    lo = cmin + ((uint64_t)b << shift);
+    const uint64_t top = lo + ((1ull << shift) - 1ull);
+    hi = top < cmax ? top : cmax;
+    if (cnt <= 32) break;
+    // narrow to the min/max of the crossing bin's entries
+    uint64_t a = ~0ull, z = 0;
+    for (int idx = lane; idx < k; idx += 32) {
+      const uint64_t key = key_of(idx);
+      if (key >= lo && key <= hi) {
+        a = key < a ? key : a;
+        z = key > z ? key : z;
+      }
+    }
+    cmin = warp_min_u64(a);
+    cmax = warp_max_u64(z);
+  }
+
+  // 4. final pass: lower bounds everywhere, full gaps below the candidates,
   // candidates compacted (or summed when they share one key).
   uint64_t acc = 0, gsum = 0;
   unsigned pos = 0;
+  int first_cand = -1;
   const unsigned lt = (1u << lane) - 1u;
   for (int base = 0; base < k; base += 32) {
     const int idx = base + lane;
@@ -286,40 +361,51 @@ __device__ uint64_t column_q(const int32_t* rows, const ulonglong2* lg, unsigned
     const bool below = all_below || key < lo;
     const bool cand = valid && !all_below && key >= lo && key <= hi;
     if (valid) acc += __umul64hi(pess ? key : (kOne - key), below ? b.x + b.y : b.x);
+    const unsigned m = __ballot_sync(kFull, cand);
+    if (m && first_cand < 0) first_cand = base + __ffs(m) - 1;
     if (!uniform) {
-      const unsigned m = __ballot_sync(kFull, cand);
       if (cand) {
         const unsigned at = pos + __popc(m & lt);
         ws->ck[at] = key;
-        ws->cg[at] = b.y;
+        ws->cg[at] = b.y < rem ? b.y : rem;
+        ws->ci[at] = idx;
       }
       pos += __popc(m);
     } else if (cand) {
-      gsum += b.y;
+      gsum = sat_add(gsum, b.y < rem ? b.y : rem);
     }
   }
   acc = warp_sum_u64(acc);
-  if (all_below || rem == 0) return acc;
+  if (all_below) {
+    *hint_out = -1;
+    return acc;
+  }
   const uint64_t r2 = rem - fb;  // > 0 by construction of the crossing bin
   if (uniform) {
     // one key for all candidates: they take min(r2, their total gap) together
-    const uint64_t g = warp_sum_u64(gsum);
+    const uint64_t g = warp_sum_sat(gsum);
+    *hint_out = first_cand;
     return acc + __umul64hi(pess ? lo : (kOne - lo), g < r2 ? g : r2);
   }
   __syncwarp();
   // Resolve the <= 32 candidates exactly: candidate i takes its gap clipped to
-  // what the candidates ordered before it (by key, then list position) leave.
+  // what the candidates ordered before it (by key, then list position) leave;
+  // the one that takes the last of r2 is the threshold.
   uint64_t extra = 0;
+  int thr = -1;
   if (lane < (int)pos) {
     const uint64_t ki = ws->ck[lane], gi = ws->cg[lane];
     uint64_t before = 0;
     for (unsigned j = 0; j < pos; ++j) {
       const uint64_t kj = ws->ck[j];
-      if (kj < ki || (kj == ki && j < (unsigned)lane)) before += ws->cg[j];
+      if (kj < ki || (kj == ki && j < (unsigned)lane)) before = sat_add(before, ws->cg[j]);
     }
     const uint64_t left = r2 > before ? r2 - before : 0;
     extra = __umul64hi(pess ? ki : (kOne - ki), gi < left ? gi : left);
+    if (left > 0 && left <= gi) thr = ws->ci[lane];
   }
+  const unsigned tm = __ballot_sync(kFull, thr >= 0);
+  *hint_out = tm ? __shfl_sync(kFull, thr, __ffs(tm) - 1) : -1;
   __syncwarp();
   return acc + warp_sum_u64(extra);
 }
@@ -454,9 +540,15 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
             const int32_t c = T.c0 + ls;
             const int32_t eb = T.e0 & ~3, cb = T.c0 & ~3, mb = T.c0 & ~1;
             const int32_t ca = st.cptr[c - cb], ce = st.cptr[c + 1 - cb];
+            const int32_t h = P.hint ? P.hint[c] : -1;
+            int32_t hout;
             const uint64_t q = column_q(st.rows + (ca - eb), st.lg + (ca - T.e0), st.keys + (ca - T.e0), ce - ca,
-                                        st.rem[c - mb], P.V[(k_iter - 1) & 1], P.pessimistic != 0, ws, lane);
-            if (lane == 0) st.q[ls] = q;
+                                        st.rem[c - mb], P.V[(k_iter - 1) & 1], P.pessimistic != 0, ws, lane, h,
+                                        &hout);
+            if (lane == 0) {
+              st.q[ls] = q;
+              if (P.hint && hout != h) P.hint[c] = hout;
+            }
           } else {
             // one state too large for a stage: this warp reads its columns from global memory
             const Problem& P = L.probs[T.p];
@@ -466,8 +558,11 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
             int32_t best = -1;
             for (int32_t cc = T.c0; cc < T.c1; ++cc) {
               const int32_t ca = __ldg(P.colptr + cc), ce = __ldg(P.colptr + cc + 1);
+              const int32_t h = P.hint ? P.hint[cc] : -1;
+              int32_t hout;
               const uint64_t q = column_q(P.rowval + ca, P.lg + ca, nullptr, ce - ca, __ldg(P.rem + cc), Vin, pess,
-                                          ws, lane);
+                                          ws, lane, h, &hout);
+              if (lane == 0 && P.hint && hout != h) P.hint[cc] = hout;
               if (best < 0 || (P.maximize ? q > bestq : q < bestq)) {
                 bestq = q;
                 best = cc - T.c0;
@@ -518,7 +613,15 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
                     }
                   }
                 }
-                vnew = bestq >= (kOne >> 1) ? kOne : (bestq << 1);  // Q2.62 -> Q1.63, clamp at 1
+                if (P.property == kPropReward) {
+                  // W_k = c_s + gamma * T(W_{k-1}) in signed Q2.62, clamped to [0, 1]
+                  const int64_t t = (int64_t)(__umul64hi(P.gamma_fix, bestq) << 1);
+                  int64_t w = P.rbias[s] + t;
+                  w = w < 0 ? 0 : (w > (int64_t)(kOne >> 1) ? (int64_t)(kOne >> 1) : w);
+                  vnew = (uint64_t)w << 1;
+                } else {
+                  vnew = bestq >= (kOne >> 1) ? kOne : (bestq << 1);  // Q2.62 -> Q1.63, clamp at 1
+                }
               }
               finish_state(P, s, k_iter, vnew, best, Vin, Vout, dmax);
             }

@@ -79,7 +79,8 @@ struct alignas(16) Problem {
   const uint8_t* fixed;   // n_states: 0 free, 1 held at 1 (reach target), 2 held at 0 (avoid)
   uint64_t* V[2];         // ping-pong value buffers; iteration k writes V[k & 1]
   int32_t* policy;        // nullable; see policy_mode
-  const uint64_t* rbias;  // reward: per-state additive term (normalised), nullable
+  const int64_t* rbias;   // reward: per-state term c_s of W_k = c_s + gamma T(W_{k-1}), signed Q2.62
+  int32_t* hint;          // per column: entry that held the O-maximization threshold last iteration (-1: none)
   int32_t n_states;
   int32_t pessimistic;
   int32_t maximize;
@@ -148,6 +149,10 @@ struct Session {
   std::vector<Problem> probs_h;
   std::vector<int32_t> base_h;
   std::vector<int64_t> policy_cells;
+  std::vector<double> v_offset, v_scale;  // V = offset + scale * W (reward: affine map; reach: 0, 1)
+  std::vector<uint64_t*> w0;              // reward: device copy of W_0 for resets (nullptr otherwise)
+  int32_t* hints = nullptr;               // sum of n_cols: threshold hints of every problem
+  int64_t total_cols = 0;
   int32_t max_horizon = 0;
   bool any_infinite = false;
   uint8_t* fixed = nullptr;

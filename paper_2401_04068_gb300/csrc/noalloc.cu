@@ -108,6 +108,10 @@ extern "C" IMDP_API imdp_status imdp_value_iteration_noalloc(imdp_model* m, cons
   }
   imdp_status s = check_spec(dm, spec);
   if (s != IMDP_OK) return s;
+  if (spec->property == IMDP_REWARD) {
+    set_error("imdp_value_iteration_noalloc: reward properties are not offered here");
+    return IMDP_EINVAL;
+  }
   const int32_t n_avoid = spec->property == IMDP_REACH_AVOID ? spec->n_avoid : 0;
   if ((int64_t)spec->n_reach + n_avoid > kNoAllocMaxStates) {
     set_error("imdp_value_iteration_noalloc: more than 131072 reach + avoid indices");

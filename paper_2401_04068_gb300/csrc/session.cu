@@ -3,6 +3,7 @@
 // and the export of (V, k, residual, policy) as value_iteration returns them
 // (Sec. 3.2).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -19,18 +20,41 @@ __global__ void init_values_kernel(int64_t n, const uint8_t* __restrict__ fixed,
     V0[i] = fixed[i] == 1 ? kOne : 0ull;
 }
 
-// V (Q1.63) -> binary64; with `prev`, writes V - prev (the Bellman residual).
+// W (Q1.63) -> V = offset + scale * W in binary64; with `prev`, writes
+// scale * (W - prev), the Bellman residual V_k - V_{k-1}.
 __global__ void export_values_kernel(int32_t n, const uint64_t* __restrict__ V, const uint64_t* __restrict__ prev,
-                                     double* __restrict__ out) {
-  const double scale = 1.0 / 9223372036854775808.0;
+                                     double offset, double scale_v, double* __restrict__ out) {
+  const double scale = scale_v / 9223372036854775808.0;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (prev) {
       const uint64_t a = V[i], b = prev[i];
       out[i] = a >= b ? (double)(a - b) * scale : -(double)(b - a) * scale;
     } else {
-      out[i] = (double)V[i] * scale;
+      out[i] = offset + (double)V[i] * scale;
     }
   }
+}
+
+// Affine map of a reward problem into [0, 1] (V = lo + D W). Rewards r, discount
+// g, horizon K: if V_{k-1} lies in [a, b], the averaging operator keeps
+// T(V_{k-1}) in [a, b], so V_k = r + g T(V_{k-1}) lies in [rmin + g a, rmax + g b];
+// from V_0 = r this gives V_k in [rmin A_k, rmax A_k] with A_k = sum_{i<=k} g^i,
+// and every V_k, k <= K, lies in [min(rmin, rmin A), max(rmax, rmax A)].
+void reward_map(const double* r, int32_t n, double g, int32_t K, bool infinite, double* lo, double* D) {
+  double rmin = r[0], rmax = r[0];
+  for (int32_t s = 1; s < n; ++s) {
+    rmin = r[s] < rmin ? r[s] : rmin;
+    rmax = r[s] > rmax ? r[s] : rmax;
+  }
+  double A;
+  if (infinite) A = 1.0 / (1.0 - g);
+  else if (g == 1.0) A = (double)K + 1.0;
+  else A = (1.0 - std::pow(g, (double)K + 1.0)) / (1.0 - g);
+  const double a = std::min(rmin, rmin * A), b = std::max(rmax, rmax * A);
+  // widen by a relative margin so rounding never pushes W outside [0, 1]
+  const double span = b - a, pad = 1e-9 * (span > 0 ? span : 1.0) + 1e-300;
+  *lo = a - pad;
+  *D = (span > 0 ? span : 1.0) + 2 * pad;
 }
 
 __global__ void fill_i32_kernel(int64_t n, int32_t* p, int32_t v) {
@@ -57,7 +81,15 @@ imdp_status check_spec(const DevModel* m, const imdp_spec* sp) {
     set_error("unknown property"); return IMDP_EINVAL;
   }
   if (sp->property == IMDP_REWARD) {
-    set_error("reward properties are not supported by this build"); return IMDP_EINVAL;
+    // Sec. 3.2: rewards per state, discount in (0, 1] (strictly below 1 for an infinite horizon)
+    if (!sp->reward) { set_error("reward property needs a reward vector"); return IMDP_EINVAL; }
+    if (!(sp->discount > 0.0) || !(sp->discount <= 1.0) || (sp->infinite_time && !(sp->discount < 1.0))) {
+      set_error("discount must be in (0, 1] (finite horizon) or (0, 1) (infinite horizon)"); return IMDP_EINVAL;
+    }
+    for (int32_t s = 0; s < m->n_states; ++s)
+      if (!(sp->reward[s] == sp->reward[s]) || sp->reward[s] > 1e300 || sp->reward[s] < -1e300) {
+        set_error("rewards must be finite"); return IMDP_EINVAL;
+      }
   }
   if (sp->horizon < 0) { set_error("horizon must be >= 0"); return IMDP_EINVAL; }
   if (sp->infinite_time && !(sp->eps > 0.0)) { set_error("eps must be > 0 for an infinite horizon"); return IMDP_EINVAL; }
@@ -111,7 +143,8 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   for (int p = 0; p < count; ++p) {
     const imdp_spec* sp = specs[p];
     uint8_t* f = fixed.data() + S->base_h[p];
-    for (int32_t i = 0; i < sp->n_reach; ++i) f[sp->reach[i]] = 1;
+    if (sp->property != IMDP_REWARD)
+      for (int32_t i = 0; i < sp->n_reach; ++i) f[sp->reach[i]] = 1;
     if (sp->property == IMDP_REACH_AVOID)
       for (int32_t i = 0; i < sp->n_avoid; ++i) {
         if (f[sp->avoid[i]] == 1) { delete S; set_error("a state is in both the reach and the avoid set"); return IMDP_EINVAL; }
@@ -119,6 +152,9 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
       }
     max_class = std::max(max_class, choose_col_class(ms[p]->max_col));
   }
+  S->v_offset.assign(count, 0.0);
+  S->v_scale.assign(count, 1.0);
+  S->w0.assign(count, nullptr);
   std::vector<Tile> tiles;
   for (int p = 0; p < count; ++p) {
     const size_t at = tiles.size();
@@ -127,17 +163,20 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   }
   S->n_tiles = (int32_t)tiles.size();
   S->tiles = S->alloc<Tile>(tiles.size());
+  for (int p = 0; p < count; ++p) S->total_cols += ms[p]->n_cols;
+  S->hints = S->alloc<int32_t>((size_t)S->total_cols);
   S->fixed = S->alloc<uint8_t>(padded_u8(total));
   S->V = S->alloc<uint64_t>(2 * total);
   S->base = S->alloc<int32_t>(count + 1);
   S->probs = S->alloc<Problem>(count);
   S->its = S->alloc<IterState>(count);
   S->ctl = S->alloc<StepControl>(1);
-  if (!S->tiles || !S->fixed || !S->V || !S->base || !S->probs || !S->its || !S->ctl) {
+  if (!S->hints || !S->tiles || !S->fixed || !S->V || !S->base || !S->probs || !S->its || !S->ctl) {
     delete S; set_error("device allocation failed (session)"); return IMDP_ENOMEM;
   }
   S->probs_h.resize(count);
   S->policy_cells.assign(count, 0);
+  int64_t col_off = 0;
   for (int p = 0; p < count; ++p) {
     DevModel* m = ms[p];
     const imdp_spec* sp = specs[p];
@@ -149,6 +188,8 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
     P.lg = m->lg;
     P.rem = m->rem;
     P.fixed = S->fixed + S->base_h[p];
+    P.hint = S->hints + col_off;
+    col_off += m->n_cols;
     P.V[0] = S->V + S->base_h[p];
     P.V[1] = S->V + total + S->base_h[p];
     P.n_states = m->n_states;
@@ -158,6 +199,34 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
     P.infinite = sp->infinite_time ? 1 : 0;
     P.horizon = sp->infinite_time ? (sp->horizon > 0 ? sp->horizon : 1000000) : sp->horizon;
     P.eps_fix = sp->infinite_time ? eps_to_fixed(sp->eps) : 0;
+    if (sp->property == IMDP_REWARD) {
+      const int32_t n = m->n_states;
+      double lo, D;
+      reward_map(sp->reward, n, sp->discount, P.horizon, P.infinite != 0, &lo, &D);
+      S->v_offset[p] = lo;
+      S->v_scale[p] = D;
+      std::vector<int64_t> c(n);
+      std::vector<uint64_t> w(n);
+      const double g = sp->discount;
+      for (int32_t s = 0; s < n; ++s) {
+        // W_k = c_s + g T(W_{k-1}),  c_s = (r_s - lo (1 - g)) / D  (signed Q2.62)
+        const double cs = (sp->reward[s] - lo * (1.0 - g)) / D;
+        c[s] = (int64_t)std::llround(cs * 4611686018427387904.0);
+        const double ws = std::min(1.0, std::max(0.0, (sp->reward[s] - lo) / D));
+        w[s] = (uint64_t)std::llround(ws * 4611686018427387904.0) << 1;
+      }
+      int64_t* d_c = S->alloc<int64_t>(n);
+      uint64_t* d_w = S->alloc<uint64_t>(n);
+      if (!d_c || !d_w) { delete S; set_error("device allocation failed (reward)"); return IMDP_ENOMEM; }
+      cudaError_t er = cudaMemcpyAsync(d_c, c.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st);
+      if (er == cudaSuccess) er = cudaMemcpyAsync(d_w, w.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st);
+      if (er == cudaSuccess) er = cudaStreamSynchronize(st);
+      if (er != cudaSuccess) { delete S; return cuda_status(er, "reward setup"); }
+      P.rbias = d_c;
+      S->w0[p] = d_w;
+      P.gamma_fix = g >= 1.0 ? kOne : (uint64_t)std::llround(g * 9223372036854775808.0);
+      if (P.infinite) P.eps_fix = eps_to_fixed(sp->eps / D);
+    }
     S->max_horizon = std::max(S->max_horizon, P.horizon);
     S->any_infinite = S->any_infinite || P.infinite;
     if (want_policy && want_policy[p]) {
@@ -195,6 +264,10 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
 imdp_status Session::reset(cudaStream_t st) {
   init_values_kernel<<<(int)std::min<int64_t>((total + 255) / 256, 8192), 256, 0, st>>>(total, fixed, V);
   cudaError_t e = cudaGetLastError();
+  for (int p = 0; p < count && e == cudaSuccess; ++p)
+    if (w0[p]) e = cudaMemcpyAsync(probs_h[p].V[0], w0[p], sizeof(uint64_t) * probs_h[p].n_states,
+                                   cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(hints, 0xff, sizeof(int32_t) * (size_t)total_cols, st);  // -1: no hint
   if (e == cudaSuccess) e = cudaMemsetAsync(its, 0, sizeof(IterState) * count, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(StepControl), st);
   for (int p = 0; p < count && e == cudaSuccess; ++p)
@@ -296,7 +369,7 @@ imdp_status Session::read(int32_t p, double* V_out, int32_t* k_out, double* res_
       dst = (double*)t;
     }
     if (prev == nullptr || k >= 1) {
-      export_values_kernel<<<g, 256, 0, st>>>(n, Vk, prev, dst);
+      export_values_kernel<<<g, 256, 0, st>>>(n, Vk, prev, v_offset[p], v_scale[p], dst);
     } else {
       cudaMemsetAsync(dst, 0, sizeof(double) * n, st);
     }

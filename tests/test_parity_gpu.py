@@ -235,3 +235,100 @@ def test_full_size_sampled_one_step(name):
             qs.append(oracle.omax_column(Vprev[m.rowval[a:b]], m.lower[a:b], m.upper[a:b], True)[0])
         assert abs(V[s] - max(qs)) <= 1e-12, (s, V[s], qs)
         assert abs(qs[pol[0][s]] - max(qs)) <= 1e-12
+
+
+# --------------------------------------------------------------------------- discounted reward (Sec. 3.2)
+
+def _reward_tol(oV):
+    return TOL_F64 * max(1.0, float(np.max(np.abs(oV))))
+
+
+@pytest.mark.parametrize("pess,maxi", MODES)
+@pytest.mark.parametrize("gamma,K", [(0.9, 30), (0.95, 100), (1.0, 12)])
+def test_finite_reward(pess, maxi, gamma, K):
+    m = banded_imdp(300, 2, 300 * 2 * 14 + 1, eps=0.1, seed=40)
+    r = np.random.default_rng(1).uniform(-1.0, 3.0, m.n_states)
+    model = _model(m)
+    st, V, k, res, pol = g.value_iteration(model, m.n_states, policy=True, property=g.IMDP_REWARD, horizon=K,
+                                           reward=r, discount=gamma, pessimistic=pess, maximize=maxi)
+    ost, oV, ok, ores, _ = run_oracle(m, property=oracle.REWARD, horizon=K, reward=r, discount=gamma,
+                                      pessimistic=pess, maximize=maxi)
+    assert st == ost == "ok" and k == ok == K
+    tol = _reward_tol(oV)
+    np.testing.assert_allclose(V, oV, rtol=0, atol=tol)
+    np.testing.assert_allclose(res, ores, rtol=0, atol=tol)
+    # policy: the chosen action attains the optimum of r + gamma * q
+    q = q_values(m, V - res, pess)
+    for s in range(0, m.n_states, 7):
+        js = range(m.stateptr[s], m.stateptr[s + 1])
+        qs = np.array([q[j] for j in js])
+        best = qs.max() if maxi else qs.min()
+        assert abs(qs[pol[0][s]] - best) * gamma <= tol
+
+
+def test_infinite_reward_and_closed_form():
+    m = banded_imdp(200, 2, 200 * 2 * 10 + 1, eps=0.05, seed=41)
+    r = np.random.default_rng(2).uniform(0.0, 2.0, m.n_states)
+    model = _model(m)
+    st, V, k, res, _ = g.value_iteration(model, m.n_states, property=g.IMDP_REWARD, infinite_time=True, eps=1e-9,
+                                         horizon=100000, reward=r, discount=0.9)
+    ost, oV, ok, _, _ = run_oracle(m, property=oracle.REWARD, infinite_time=True, eps=1e-9, horizon=100000,
+                                   reward=r, discount=0.9)
+    assert st == ost == "ok"
+    assert abs(k - ok) <= 1  # the stopping iteration may differ by one at the eps boundary
+    np.testing.assert_allclose(V, oV, rtol=0, atol=1e-7)
+    # the sink is absorbing with reward r_sink: V = r / (1 - gamma)
+    s = int(m.sink[0])
+    assert V[s] == pytest.approx(r[s] / 0.1, rel=1e-7)
+
+
+def test_reward_batch_mixed_with_reachability():
+    m = banded_imdp(150, 2, 150 * 2 * 8 + 1, seed=42)
+    r = np.linspace(-2.0, 2.0, m.n_states)
+    model = _model(m)
+    specs = [g.make_spec(property=g.IMDP_REWARD, horizon=20, reward=r, discount=0.8),
+             g.make_spec(horizon=25, reach=m.goal)]
+    outs = [np.zeros(m.n_states), np.zeros(m.n_states)]
+    ks = [0, 0]
+    g.imdp_value_iteration_batch([model, model], specs, outs, ks)
+    assert ks == [20, 25]
+    _, oV, _, _, _ = run_oracle(m, property=oracle.REWARD, horizon=20, reward=r, discount=0.8)
+    np.testing.assert_allclose(outs[0], oV, rtol=0, atol=_reward_tol(oV))
+    _, oV2, _, _, _ = run_oracle(m, horizon=25, reach=m.goal)
+    np.testing.assert_allclose(outs[1], oV2, rtol=0, atol=TOL_F64)
+
+
+# --------------------------------------------------------------------------- wide intervals, resets
+
+@pytest.mark.parametrize("k_mean,n_dom", [(40, 200), (300, 900), (3500, 3600)])
+def test_wide_intervals_sum_of_upper_far_above_one(k_mean, n_dom):
+    # upper = 1 on every entry: a column's upper bounds add up to k (gap sums
+    # far beyond 2 in fixed point); the last case has columns longer than a
+    # shared-memory tile (read from global memory)
+    m = banded_imdp(n_dom, 1, n_dom * (k_mean + 1) + 1, eps=0.1, seed=k_mean)
+    m.upper = np.ones_like(m.upper)
+    m.lower = m.lower * 0.5
+    model = _model(m)
+    for pess, maxi in MODES:
+        _compare(m, model, horizon=6, reach=m.goal, pessimistic=pess, maximize=maxi)
+
+
+def test_session_reset_restarts_from_v0():
+    m = banded_imdp(300, 2, 300 * 2 * 20 + 1, seed=13)
+    model = _model(m)
+    spec = g.make_spec(horizon=40, reach=m.goal)
+    sess = g.imdp_session_create([model], [spec])
+    V1 = np.zeros(m.n_states)
+    V2 = np.zeros(m.n_states)
+    g.imdp_session_run(sess)
+    g.imdp_session_read(sess, 0, V1)
+    g.imdp_session_reset(sess)
+    g.imdp_session_step(sess, 17)
+    g.imdp_session_reset(sess)
+    g.imdp_session_run(sess)
+    k = [0]
+    g.imdp_session_read(sess, 0, V2, k)
+    assert k[0] == 40
+    np.testing.assert_array_equal(V1, V2)
+    _, oV, _, _, _ = run_oracle(m, horizon=40, reach=m.goal)
+    np.testing.assert_allclose(V2, oV, atol=TOL_F64)
