@@ -6,9 +6,9 @@
 // Data movement. The launch is persistent (one CTA per SM). The model is cut into
 // state-aligned tiles (consecutive states of one problem, <= kTileEntries
 // entries). A producer warp streams each tile's destination indices and bound
-// pairs into a two-stage shared-memory ring with bulk asynchronous copies
-// (cp.async.bulk, completion counted on an mbarrier), while eight consumer warps
-// work on the previous tile. Every entry crosses HBM once per iteration.
+// pairs into a three-stage shared-memory ring with bulk asynchronous copies
+// (cp.async.bulk, completion counted on an mbarrier), while twelve consumer warps
+// work on the tiles already landed. Every entry crosses HBM once per iteration.
 //
 // O-maximization without a sort. For a pessimistic adversary the procedure of
 // Sec. 4 orders the destinations by ascending V, starts from p = lower and hands
@@ -50,7 +50,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBins = 64;
 constexpr int kConsumerWarps = 12;
-constexpr int kStages = 2;
+constexpr int kStages = 3;
 constexpr int kBlockThreads = 32 * (kConsumerWarps + 1);
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz: bound of every wait
 
@@ -69,7 +69,6 @@ struct WarpScratch {
 struct Stage {
   int32_t rows[kTileEntries + 8];        // destinations
   ulonglong2 lg[kTileEntries];           // {lower, gap}
-  unsigned long long keys[kTileEntries]; // keys of the running iteration
   unsigned long long q[kTileCols];       // per-column O-maximization values
   unsigned long long rem[kTileCols + 4]; // 1 - sum(lower) per column
   int32_t sptr[kTileStates + 8];         // stateptr window
@@ -197,31 +196,22 @@ __device__ __forceinline__ uint64_t warp_excl_scan_sat(uint64_t x, int lane) {
 
 // ---------------------------------------------------------------- one column
 
-// Entries [0, k) of one column: destinations `rows`, bound pairs `lg`, key
-// scratch `keys` (shared memory; nullptr = recompute keys from V on every pass,
-// used when the column is read straight from global memory). `hint` is the entry
-// that held the threshold in the previous iteration (-1: none); the entry that
-// holds it now is returned in *hint_out. Returns q in Q2.62.
-__device__ uint64_t column_q(const int32_t* rows, const ulonglong2* lg, unsigned long long* keys, int32_t k,
-                             uint64_t rem, const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane,
-                             int32_t hint, int32_t* hint_out) {
+// Entries [0, k) of one column: destinations `rows`, bound pairs `lg` (shared
+// or global memory). Keys are recomputed from V on every pass (V is read
+// through L1). `hint` is the entry that held the threshold in the previous
+// iteration (-1: none); the entry that holds it now is returned in *hint_out.
+// Returns q in Q2.62.
+__device__ uint64_t column_q(const int32_t* rows, const ulonglong2* lg, int32_t k, uint64_t rem,
+                             const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane, int32_t hint,
+                             int32_t* hint_out) {
   auto key_of = [&](int idx) -> uint64_t {
-    if (keys) return keys[idx];
     const uint64_t v = __ldg(V + rows[idx]);
     return pess ? v : (kOne - v);
   };
-  // 1. keys (stored in shared memory for the later passes)
-  if (keys) {
-#pragma unroll 4
-    for (int idx = lane; idx < k; idx += 32) {
-      const uint64_t v = __ldg(V + rows[idx]);
-      keys[idx] = pess ? v : (kOne - v);
-    }
-    __syncwarp();
-  }
 
   if (rem == 0) {  // nothing to hand out: every entry keeps its lower bound
     uint64_t acc = 0;
+#pragma unroll 4
     for (int idx = lane; idx < k; idx += 32) {
       const uint64_t key = key_of(idx);
       acc += __umul64hi(pess ? key : (kOne - key), lg[idx].x);
@@ -230,12 +220,13 @@ __device__ uint64_t column_q(const int32_t* rows, const ulonglong2* lg, unsigned
     return warp_sum_u64(acc);
   }
 
-  // 2. warm start: does last iteration's threshold entry still hold it? With
+  // 1. warm start: does last iteration's threshold entry still hold it? With
   // kappa its key, it does exactly when F(< kappa) < rem <= F(<= kappa), F being
-  // the gap sum; then one pass gives q.
+  // the gap sum; then this one pass gives q.
   if (hint >= 0 && hint < k) {
     const uint64_t kap = key_of(hint);
     uint64_t acc = 0, flt = 0, geq = 0;
+#pragma unroll 4
     for (int idx = lane; idx < k; idx += 32) {
       const uint64_t key = key_of(idx);
       const ulonglong2 b = lg[idx];
@@ -257,14 +248,16 @@ __device__ uint64_t column_q(const int32_t* rows, const ulonglong2* lg, unsigned
     }
   }
 
-  // 3. threshold search: after it, keys < lo are below (full gap), keys > hi are
-  // above (lower bound), keys in [lo, hi] are candidates sharing rem - fb.
+  // 2. key range
   uint64_t lmin = ~0ull, lmax = 0;
+#pragma unroll 4
   for (int idx = lane; idx < k; idx += 32) {
     const uint64_t key = key_of(idx);
     lmin = key < lmin ? key : lmin;
     lmax = key > lmax ? key : lmax;
   }
+  // 3. threshold search: after it, keys < lo are below (full gap), keys > hi are
+  // above (lower bound), keys in [lo, hi] are candidates sharing rem - fb.
   uint64_t lo = 0, hi = kOne, fb = 0;
   bool all_below = false, uniform = false;
   uint64_t cmin = warp_min_u64(lmin), cmax = warp_max_u64(lmax);
@@ -542,9 +535,8 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
             const int32_t ca = st.cptr[c - cb], ce = st.cptr[c + 1 - cb];
             const int32_t h = P.hint ? P.hint[c] : -1;
             int32_t hout;
-            const uint64_t q = column_q(st.rows + (ca - eb), st.lg + (ca - T.e0), st.keys + (ca - T.e0), ce - ca,
-                                        st.rem[c - mb], P.V[(k_iter - 1) & 1], P.pessimistic != 0, ws, lane, h,
-                                        &hout);
+            const uint64_t q = column_q(st.rows + (ca - eb), st.lg + (ca - T.e0), ce - ca, st.rem[c - mb],
+                                        P.V[(k_iter - 1) & 1], P.pessimistic != 0, ws, lane, h, &hout);
             if (lane == 0) {
               st.q[ls] = q;
               if (P.hint && hout != h) P.hint[c] = hout;
@@ -560,8 +552,8 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
               const int32_t ca = __ldg(P.colptr + cc), ce = __ldg(P.colptr + cc + 1);
               const int32_t h = P.hint ? P.hint[cc] : -1;
               int32_t hout;
-              const uint64_t q = column_q(P.rowval + ca, P.lg + ca, nullptr, ce - ca, __ldg(P.rem + cc), Vin, pess,
-                                          ws, lane, h, &hout);
+              const uint64_t q = column_q(P.rowval + ca, P.lg + ca, ce - ca, __ldg(P.rem + cc), Vin, pess, ws, lane,
+                                          h, &hout);
               if (lane == 0 && P.hint && hout != h) P.hint[cc] = hout;
               if (best < 0 || (P.maximize ? q > bestq : q < bestq)) {
                 bestq = q;
