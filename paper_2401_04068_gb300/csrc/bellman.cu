@@ -49,19 +49,27 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBins = 64;
-constexpr int kConsumerWarps = 12;
+constexpr int kConsumerWarps = 16;
 constexpr int kStages = 3;
 constexpr int kBlockThreads = 32 * (kConsumerWarps + 1);
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz: bound of every wait
 
+// Per-warp scratch. The histogram is dead by the time the candidate list is
+// written (the list is filled in the final pass), so the two share storage.
 struct WarpScratch {
-  unsigned int hl[kBins];        // gap sum per bin, low 32 bits (wraps)
-  unsigned int hh[kBins];        // gap sum per bin, high 32 bits plus the low part's carries
-  unsigned int hc[kBins];        // entry count per bin
-  unsigned int hsat[2];          // bins whose sum passed 2^64 (saturated)
-  int ci[32];                    // compacted candidates: entry index
-  unsigned long long ck[32];     // compacted candidates: key
-  unsigned long long cg[32];     //                       gap
+  union {
+    struct {
+      unsigned int hl[kBins];    // gap sum per bin, low 32 bits (wraps)
+      unsigned int hh[kBins];    // gap sum per bin, high 32 bits plus the low part's carries
+      unsigned int hc[kBins];    // entry count per bin
+      unsigned int hsat[2];      // bins whose sum passed 2^64 (saturated)
+    };
+    struct {
+      unsigned long long ck[32]; // compacted candidates: key
+      unsigned long long cg[32]; //                       gap
+      int ci[32];                //                       entry index
+    };
+  };
 };
 
 // One ring stage: a tile's data and metadata, each array a 16-byte-aligned
