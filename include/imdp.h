@@ -220,6 +220,33 @@ IMDP_API int64_t imdp_session_launches(const imdp_session* s);
 
 IMDP_API void imdp_session_destroy(imdp_session* s);
 
+/*
+ * Continuous-batching server. Requests (a resident model plus a specification)
+ * share the Bellman launches of one slotted batch run by a worker thread: a
+ * request is admitted when a slot (up to 1024) and enough of the server's device
+ * memory budget are free, joins the running batch between chunks of 8
+ * iterations, and retires on its own horizon or convergence test. Each result
+ * equals what imdp_value_iteration returns for the same request alone.
+ *   hbm_budget   bytes of device memory for per-request state (values, masks,
+ *                hints, outputs); allocated once at creation (>= 1 MiB)
+ * Thread-safe: submit/poll/wait may be called from any thread. Models must
+ * outlive their requests. Policies are not produced by the server.
+ */
+typedef struct imdp_server imdp_server;
+IMDP_API imdp_status imdp_server_create(size_t hbm_budget, imdp_server** out);
+/* Queue a request; returns at once with a ticket. IMDP_ENOMEM if the request
+ * alone exceeds the budget, IMDP_EBUSY if the queue is full. */
+IMDP_API imdp_status imdp_server_submit(imdp_server* s, imdp_model* m, const imdp_spec* spec, uint64_t* ticket);
+/* Result of a finished request (then the ticket is released): V_out double[n]
+ * (host or device), k_out iterations, latency_ms from submit to completion.
+ * IMDP_EPENDING while it runs, IMDP_ENOTFOUND for an unknown ticket. */
+IMDP_API imdp_status imdp_server_poll(imdp_server* s, uint64_t ticket, double* V_out, int32_t* k_out,
+                                      double* latency_ms);
+/* poll after waiting up to timeout_ms for the request (IMDP_ETIMEOUT if it is still running). */
+IMDP_API imdp_status imdp_server_wait(imdp_server* s, uint64_t ticket, double timeout_ms, double* V_out,
+                                      int32_t* k_out, double* latency_ms);
+IMDP_API void imdp_server_destroy(imdp_server* s);
+
 #ifdef __cplusplus
 }
 #endif

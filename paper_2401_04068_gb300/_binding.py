@@ -28,6 +28,7 @@ EXPORTED = [
     "imdp_model_destroy", "imdp_model_info", "imdp_value_iteration", "imdp_value_iteration_batch",
     "imdp_session_create", "imdp_session_reset", "imdp_session_step", "imdp_session_run", "imdp_session_read",
     "imdp_session_launches", "imdp_session_destroy", "imdp_value_iteration_noalloc",
+    "imdp_server_create", "imdp_server_submit", "imdp_server_poll", "imdp_server_wait", "imdp_server_destroy",
 ]
 
 
@@ -97,6 +98,16 @@ def load(path: Optional[str] = None):
     lib.imdp_session_destroy.restype = None
     lib.imdp_value_iteration_noalloc.argtypes = [vp, C.POINTER(imdp_spec), vp, C.POINTER(C.c_int32), vp]
     lib.imdp_value_iteration_noalloc.restype = C.c_int
+    lib.imdp_server_create.argtypes = [C.c_size_t, C.POINTER(vp)]
+    lib.imdp_server_create.restype = C.c_int
+    lib.imdp_server_submit.argtypes = [vp, vp, C.POINTER(imdp_spec), C.POINTER(C.c_uint64)]
+    lib.imdp_server_submit.restype = C.c_int
+    lib.imdp_server_poll.argtypes = [vp, C.c_uint64, vp, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+    lib.imdp_server_poll.restype = C.c_int
+    lib.imdp_server_wait.argtypes = [vp, C.c_uint64, C.c_double, vp, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+    lib.imdp_server_wait.restype = C.c_int
+    lib.imdp_server_destroy.argtypes = [vp]
+    lib.imdp_server_destroy.restype = None
     for f in ("imdp_create_csc", "imdp_create_dense", "imdp_model_info", "imdp_value_iteration",
               "imdp_value_iteration_batch", "imdp_session_create", "imdp_session_reset", "imdp_session_step",
               "imdp_session_run", "imdp_session_read"):
@@ -317,6 +328,71 @@ def imdp_value_iteration_noalloc(model: Model, spec, V_out, k_out=None, stream=N
     if check and st not in (IMDP_OK, IMDP_ENOCONV):
         _check(st, "imdp_value_iteration_noalloc")
     return st
+
+
+class Server:
+    """Owns an ``imdp_server*`` (continuous-batching request server)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        self._keep = {}  # ticket -> (model, spec) kept alive until the result is taken
+
+    def close(self):
+        if self.handle:
+            load().imdp_server_destroy(C.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def imdp_server_create(hbm_budget: int) -> Server:
+    out = C.c_void_p()
+    _check(load().imdp_server_create(int(hbm_budget), C.byref(out)), "imdp_server_create")
+    return Server(out.value)
+
+
+def imdp_server_submit(server: Server, model: Model, spec) -> int:
+    t = C.c_uint64(0)
+    _check(load().imdp_server_submit(C.c_void_p(server.handle), C.c_void_p(model.handle), C.byref(spec),
+                                     C.byref(t)), "imdp_server_submit")
+    server._keep[t.value] = (model, spec)
+    return t.value
+
+
+def imdp_server_poll(server: Server, ticket: int, V_out=None, k_out=None, latency_out=None) -> int:
+    """Returns the status: IMDP_EPENDING while the request runs."""
+    k = C.c_int32(0)
+    lat = C.c_double(0.0)
+    st = load().imdp_server_poll(C.c_void_p(server.handle), C.c_uint64(ticket), _ptr(V_out), C.byref(k), C.byref(lat))
+    if st != IMDP_EPENDING:
+        server._keep.pop(ticket, None)
+        if k_out is not None:
+            k_out[0] = k.value
+        if latency_out is not None:
+            latency_out[0] = lat.value
+    return st
+
+
+def imdp_server_wait(server: Server, ticket: int, timeout_ms: float, V_out=None, k_out=None, latency_out=None) -> int:
+    k = C.c_int32(0)
+    lat = C.c_double(0.0)
+    st = load().imdp_server_wait(C.c_void_p(server.handle), C.c_uint64(ticket), float(timeout_ms), _ptr(V_out),
+                                 C.byref(k), C.byref(lat))
+    if st not in (IMDP_ETIMEOUT,):
+        server._keep.pop(ticket, None)
+        if k_out is not None:
+            k_out[0] = k.value
+        if latency_out is not None:
+            latency_out[0] = lat.value
+    return st
+
+
+def imdp_server_destroy(server: Server):
+    server.close()
 
 
 # ---------------------------------------------------------------- convenience wrappers (host numpy in/out)

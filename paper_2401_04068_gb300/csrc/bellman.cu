@@ -230,29 +230,26 @@ __device__ uint64_t column_q(const int32_t* rows, const ulonglong2* lg, int32_t 
 
   // 1. warm start: does last iteration's threshold entry still hold it? With
   // kappa its key, it does exactly when F(< kappa) < rem <= F(<= kappa), F being
-  // the gap sum; then this one pass gives q.
+  // the gap sum; then this one pass gives q. Comparisons run on V itself:
+  // key < kappa is V < V_kappa for a pessimistic adversary, V > V_kappa for an
+  // optimistic one.
   if (hint >= 0 && hint < k) {
-    const uint64_t kap = key_of(hint);
+    const uint64_t vk = __ldg(V + rows[hint]);
     uint64_t acc = 0, flt = 0, geq = 0;
 #pragma unroll 4
     for (int idx = lane; idx < k; idx += 32) {
-      const uint64_t key = key_of(idx);
+      const uint64_t v = __ldg(V + rows[idx]);
       const ulonglong2 b = lg[idx];
-      const uint64_t v = pess ? key : (kOne - key);
-      const uint64_t g = b.y < rem ? b.y : rem;
-      if (key < kap) {
-        acc += __umul64hi(v, b.x + b.y);
-        flt = sat_add(flt, g);
-      } else {
-        acc += __umul64hi(v, b.x);
-        if (key == kap) geq = sat_add(geq, g);
-      }
+      const bool below = pess ? (v < vk) : (v > vk);
+      acc += __umul64hi(v, below ? b.x + b.y : b.x);
+      if (below) flt = sat_add(flt, b.y);
+      if (v == vk) geq = sat_add(geq, b.y);
     }
     flt = warp_sum_sat(flt);
     geq = warp_sum_sat(geq);
     if (flt < rem && rem - flt <= geq) {
       *hint_out = hint;
-      return warp_sum_u64(acc) + __umul64hi(pess ? kap : (kOne - kap), rem - flt);
+      return warp_sum_u64(acc) + __umul64hi(vk, rem - flt);
     }
   }
 

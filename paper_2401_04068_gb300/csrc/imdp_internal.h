@@ -181,6 +181,8 @@ struct Session {
   imdp_status read(int32_t p, double* V_out, int32_t* k_out, double* res_out, int32_t* pol_out, cudaStream_t st);
 };
 imdp_status check_spec(const DevModel* m, const imdp_spec* sp);
+// Affine map V = lo + D W of a reward problem (rewards r, discount g, horizon K).
+void reward_map(const double* r, int32_t n, double g, int32_t K, bool infinite, double* lo, double* D);
 
 // api.cu
 void set_error(const std::string& msg);

@@ -35,6 +35,25 @@ __global__ void export_values_kernel(int32_t n, const uint64_t* __restrict__ V, 
   }
 }
 
+
+__global__ void fill_i32_kernel(int64_t n, int32_t* p, int32_t v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// eps in Q1.63 rounded up, so an integer residual r satisfies r < eps_fix
+// exactly when r * 2^-63 < eps.
+uint64_t eps_to_fixed(double eps) {
+  if (eps >= 1.0) return kOne + 1;
+  const double x = eps * 9223372036854775808.0;
+  uint64_t f = (uint64_t)x;
+  if ((double)f < x) f += 1;
+  return f;
+}
+
+constexpr int kGraphChunk = 16;
+
+}  // namespace
+
 // Affine map of a reward problem into [0, 1] (V = lo + D W). Rewards r, discount
 // g, horizon K: if V_{k-1} lies in [a, b], the averaging operator keeps
 // T(V_{k-1}) in [a, b], so V_k = r + g T(V_{k-1}) lies in [rmin + g a, rmax + g b];
@@ -56,24 +75,6 @@ void reward_map(const double* r, int32_t n, double g, int32_t K, bool infinite, 
   *lo = a - pad;
   *D = (span > 0 ? span : 1.0) + 2 * pad;
 }
-
-__global__ void fill_i32_kernel(int64_t n, int32_t* p, int32_t v) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
-}
-
-// eps in Q1.63 rounded up, so an integer residual r satisfies r < eps_fix
-// exactly when r * 2^-63 < eps.
-uint64_t eps_to_fixed(double eps) {
-  if (eps >= 1.0) return kOne + 1;
-  const double x = eps * 9223372036854775808.0;
-  uint64_t f = (uint64_t)x;
-  if ((double)f < x) f += 1;
-  return f;
-}
-
-constexpr int kGraphChunk = 16;
-
-}  // namespace
 
 imdp_status check_spec(const DevModel* m, const imdp_spec* sp) {
   if (!sp) { set_error("spec is NULL"); return IMDP_EINVAL; }
