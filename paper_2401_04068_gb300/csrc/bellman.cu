@@ -81,9 +81,11 @@ struct Stage {
   unsigned long long rem[kTileCols + 4]; // 1 - sum(lower) per column
   int32_t sptr[kTileStates + 8];         // stateptr window
   int32_t cptr[kTileCols + 8];           // colptr window
+  int32_t hint[kTileCols + 8];           // threshold-hint window
   uint8_t fixed[kTileStates + 32];       // reach/avoid mask window
   Problem prob;                          // descriptor of the tile's problem
-  int32_t active;                        // set by the producer: the problem still runs
+  Tile tile;                             // set by the producer: the tile in this stage
+  int32_t active;                        //                      the problem still runs
   int32_t k_iter;                        //                      iteration being computed
   int32_t fixed_off;                     //                      offset of state s0 in `fixed`
   unsigned int done;                     // column slots of this tile finished so far
@@ -98,7 +100,7 @@ struct Smem {
 };
 static_assert(sizeof(int32_t) * (kTileEntries + 8) % 16 == 0, "lg must stay 16-byte aligned");
 static_assert(offsetof(Stage, rem) % 16 == 0 && offsetof(Stage, sptr) % 16 == 0 && offsetof(Stage, cptr) % 16 == 0 &&
-                  offsetof(Stage, fixed) % 16 == 0 && offsetof(Stage, prob) % 16 == 0 && sizeof(Problem) % 16 == 0,
+                  offsetof(Stage, fixed) % 16 == 0 && offsetof(Stage, prob) % 16 == 0 && offsetof(Stage, hint) % 16 == 0 && sizeof(Problem) % 16 == 0,
               "bulk-copy destinations must be 16-byte aligned");
 static_assert(sizeof(Stage) % 16 == 0, "stage alignment");
 static_assert(sizeof(Smem) <= 232448, "shared memory budget of one CTA");
@@ -468,6 +470,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
         Stage& st = S.st[stage];
         int32_t k_iter;
         const bool act = problem_active(L, T.p, &k_iter);
+        st.tile = T;
         st.active = act ? 1 : 0;
         st.k_iter = k_iter;
         if (act && !T.big) {
@@ -483,7 +486,10 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
           const uint32_t rb = (uint32_t)(ee - eb) * 4u, gb = (uint32_t)(T.e1 - T.e0) * 16u;
           const uint32_t sbytes = (uint32_t)(se - sb) * 4u, cbytes = (uint32_t)(ce - cb) * 4u;
           const uint32_t mbytes = (uint32_t)(me - mb) * 8u, fbytes = (uint32_t)(fe - fa);
-          mbar_arrive_expect_tx(&S.full[stage], rb + gb + sbytes + cbytes + mbytes + fbytes + (uint32_t)sizeof(Problem));
+          const uint32_t hbytes = P.hint ? cbytes : 0u;  // same window as colptr
+          mbar_arrive_expect_tx(&S.full[stage],
+                                rb + gb + sbytes + cbytes + mbytes + fbytes + hbytes + (uint32_t)sizeof(Problem));
+          if (hbytes) bulk_g2s(st.hint, P.hint + cb, hbytes, &S.full[stage]);
           bulk_g2s(&st.prob, &P, (uint32_t)sizeof(Problem), &S.full[stage]);
           if (sbytes) bulk_g2s(st.sptr, P.stateptr + sb, sbytes, &S.full[stage]);
           if (cbytes) bulk_g2s(st.cptr, P.colptr + cb, cbytes, &S.full[stage]);
@@ -523,8 +529,8 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
       got = __shfl_sync(kFull, got, 0);
       if (!got) break;
       (void)mbar_try_wait(&S.full[stage], round & 1);  // completed phase: acquire for every lane
-      const Tile T = L.tiles[t];
       Stage& st = S.st[stage];
+      const Tile T = st.tile;
       const int32_t nslots = T.big ? 1 : T.c1 - T.c0;
       const int32_t k_iter = st.k_iter;
       const bool active = st.active != 0;
@@ -538,7 +544,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
             const int32_t c = T.c0 + ls;
             const int32_t eb = T.e0 & ~3, cb = T.c0 & ~3, mb = T.c0 & ~1;
             const int32_t ca = st.cptr[c - cb], ce = st.cptr[c + 1 - cb];
-            const int32_t h = P.hint ? P.hint[c] : -1;
+            const int32_t h = P.hint ? st.hint[c - cb] : -1;
             int32_t hout;
             const uint64_t q = column_q(st.rows + (ca - eb), st.lg + (ca - T.e0), ce - ca, st.rem[c - mb],
                                         P.V[(k_iter - 1) & 1], P.pessimistic != 0, ws, lane, h, &hout);

@@ -101,7 +101,7 @@ size_t working_bytes(const DevModel* m, const imdp_spec* sp) {
   auto add = [&](size_t x) { b += (x + 255) & ~size_t(255); };
   add(2 * n * sizeof(uint64_t));               // V ping-pong
   add(padded_u8(n));                           // reach/avoid mask
-  add((size_t)m->n_cols * sizeof(int32_t));    // threshold hints
+  add(padded_i32(m->n_cols) * sizeof(int32_t));  // threshold hints (padded for bulk copies)
   add(n * sizeof(double));                     // exported values
   if (sp->property == IMDP_REWARD) {
     add(n * sizeof(int64_t));                  // c_s
@@ -174,7 +174,7 @@ struct Server {
     };
     uint64_t* V = (uint64_t*)take(2 * (size_t)n * sizeof(uint64_t));
     uint8_t* mask = take(padded_u8(n));
-    int32_t* hints = (int32_t*)take((size_t)m->n_cols * sizeof(int32_t));
+    int32_t* hints = (int32_t*)take(padded_i32(m->n_cols) * sizeof(int32_t));
     take((size_t)n * sizeof(double));  // export buffer (address recomputed on retire)
     Problem P;
     std::memset(&P, 0, sizeof(P));
@@ -201,7 +201,7 @@ struct Server {
     }
     cudaError_t e = cudaMemsetAsync(mask, 0, padded_u8(n), stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(mask, f.data(), n, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(hints, 0xff, (size_t)m->n_cols * sizeof(int32_t), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hints, 0xff, padded_i32(m->n_cols) * sizeof(int32_t), stream);
     if (sp->property == IMDP_REWARD) {
       int64_t* c = (int64_t*)take((size_t)n * sizeof(int64_t));
       uint64_t* w0 = (uint64_t*)take((size_t)n * sizeof(uint64_t));
@@ -287,7 +287,7 @@ struct Server {
     unsigned char* p = base + r->off;
     auto step = [&](size_t x) { return (x + 255) & ~size_t(255); };
     uint64_t* V = (uint64_t*)p;
-    double* out = (double*)(p + step(2 * (size_t)n * 8) + step(padded_u8(n)) + step((size_t)m->n_cols * 4));
+    double* out = (double*)(p + step(2 * (size_t)n * 8) + step(padded_u8(n)) + step(padded_i32(m->n_cols) * 4));
     r->result.resize(n);
     srv_export_kernel<<<std::min((n + 255) / 256, 1024), 256, 0, stream>>>(n, V + (size_t)(k & 1) * n, r->v_offset,
                                                                         r->v_scale, out);

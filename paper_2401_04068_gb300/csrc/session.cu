@@ -164,7 +164,9 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   }
   S->n_tiles = (int32_t)tiles.size();
   S->tiles = S->alloc<Tile>(tiles.size());
-  for (int p = 0; p < count; ++p) S->total_cols += ms[p]->n_cols;
+  // each problem's hint block starts on a 16-byte boundary and is padded, so
+  // the kernel's bulk copies of hint windows stay aligned and in bounds
+  for (int p = 0; p < count; ++p) S->total_cols += (int64_t)padded_i32(ms[p]->n_cols);
   S->hints = S->alloc<int32_t>((size_t)S->total_cols);
   S->fixed = S->alloc<uint8_t>(padded_u8(total));
   S->V = S->alloc<uint64_t>(2 * total);
@@ -190,7 +192,7 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
     P.rem = m->rem;
     P.fixed = S->fixed + S->base_h[p];
     P.hint = S->hints + col_off;
-    col_off += m->n_cols;
+    col_off += (int64_t)padded_i32(m->n_cols);
     P.V[0] = S->V + S->base_h[p];
     P.V[1] = S->V + total + S->base_h[p];
     P.n_states = m->n_states;
