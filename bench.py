@@ -111,6 +111,19 @@ def workload_config(name: str, m, horizon: int):
     return cfg
 
 
+def reduce_across_ranks(elapsed_ms: float, kernel_ms: float, units: float, world: int, device):
+    """Whole-job timing: the slowest rank's times (max) and every rank's units (sum).
+    Works on any process group (NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return elapsed_ms, kernel_ms, units
+    import torch
+    mx = torch.tensor([elapsed_ms, kernel_ms], dtype=torch.float64, device=device)
+    sm = torch.tensor([units], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+    return float(mx[0]), float(mx[1]), float(sm[0])
+
+
 def algorithmic_bytes_per_iteration(m) -> int:
     # rowval + lower + gap per transition; colptr + rem per column; stateptr + V read + V write per state
     return 20 * int(m.nnz) + 12 * int(m.n_cols) + 20 * int(m.n_states)
@@ -273,15 +286,7 @@ def run_ours(args, rank, world, local_rank):
     kernel_ms = sum(a.elapsed_time(b) for a, b in kev)
     launches = g.imdp_session_launches(sess) - launches0
     my_units = float(m.nnz) * args.horizon * args.steps
-    if world > 1:
-        t = torch.tensor([elapsed_ms, kernel_ms, my_units], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        torch.distributed.all_reduce(mx[:2], op=torch.distributed.ReduceOp.MAX)
-        sm = t.clone()
-        torch.distributed.all_reduce(sm[2:], op=torch.distributed.ReduceOp.SUM)
-        elapsed_ms, kernel_ms, total_units = float(mx[0]), float(mx[1]), float(sm[2])
-    else:
-        total_units = my_units
+    elapsed_ms, kernel_ms, total_units = reduce_across_ranks(elapsed_ms, kernel_ms, my_units, world, dev)
     value = total_units / (elapsed_ms / 1e3)
 
     # e2e: through the public C ABI with host buffers (pinned), copies inside the timed region
@@ -310,10 +315,7 @@ def run_ours(args, rank, world, local_rank):
             assert e2e_step() == args.horizon
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t[0])
+        e2e_s, _, _ = reduce_across_ranks(e2e_s, 0.0, 0.0, world, dev)
         e2e = {"value": float(m.nnz) * args.horizon * args.e2e_steps * world / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps}
 
