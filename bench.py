@@ -124,8 +124,11 @@ def reduce_across_ranks(elapsed_ms: float, kernel_ms: float, units: float, world
     return float(mx[0]), float(mx[1]), float(sm[0])
 
 
-def algorithmic_bytes_per_iteration(m) -> int:
-    # rowval + lower + gap per transition; colptr + rem per column; stateptr + V read + V write per state
+def algorithmic_bytes_per_iteration(m, storage: str = "f64") -> int:
+    """rowval + lower + gap per transition; colptr + rem (+ shift) per column;
+    stateptr + V read + V write per state."""
+    if storage == "f32":
+        return 12 * int(m.nnz) + 16 * int(m.n_cols) + 20 * int(m.n_states)
     return 20 * int(m.nnz) + 12 * int(m.n_cols) + 20 * int(m.n_states)
 
 
@@ -244,7 +247,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
 
     m = make_workload(args.workload, rank, args.models)
-    model = g.create_model(m, stream=stream)
+    dtype = g.IMDP_F32 if args.dtype == "f32" else g.IMDP_F64
+    model = g.create_model(m, dtype=dtype, stream=stream)
     spec = g.make_spec(horizon=args.horizon, reach=m.goal, pessimistic=True, maximize=True)
     sess = g.imdp_session_create([model], [spec], stream=stream)
 
@@ -300,7 +304,7 @@ def run_ours(args, rank, world, local_rank):
 
         def e2e_step():
             mdl = g.imdp_create_csc(m.n_states, m.n_cols, m.nnz, pin["stateptr"], pin["colptr"], pin["rowval"],
-                                    pin["lower"], pin["upper"], stream=stream)
+                                    pin["lower"], pin["upper"], dtype=dtype, stream=stream)
             kk2 = [0]
             g.imdp_value_iteration(mdl, spec, Vh, kk2, stream=stream)
             mdl.close()
@@ -322,11 +326,16 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return
     peak, peak_kind = measured_peak_hbm()
-    alg_bytes = algorithmic_bytes_per_iteration(m)
+    alg_bytes = algorithmic_bytes_per_iteration(m, args.dtype)
     launch_ms = kernel_ms / (args.steps * args.horizon)
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
-    traffic = recorded_traffic(args.workload)
+    traffic = recorded_traffic(args.workload + ("" if args.dtype == "f64" else ":f32"))
     cfg = workload_config(args.workload, m, args.horizon)
+    cfg["storage"] = "32-bit bounds (per-column scaled), 64-bit arithmetic" if args.dtype == "f32" else \
+        "64-bit bounds (Q1.63), 64-bit arithmetic"
+    if args.dtype == "f32":
+        cfg["error_bound_per_iteration"] = model.error_bound()
+        cfg["error_bound_horizon"] = model.error_bound() * args.horizon
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -358,6 +367,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="storage of the transition bounds")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)

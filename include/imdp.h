@@ -63,7 +63,10 @@ typedef enum {
 
 /* Storage precision of the transition bounds. IMDP_F64 keeps 64 bits per bound
  * (stored as unsigned fixed point with 63 fractional bits, which resolves
- * probabilities in [0, 1] to 1.1e-19 absolute, finer than binary64 near 1). */
+ * probabilities in [0, 1] to 1.1e-19 absolute, finer than binary64 near 1).
+ * IMDP_F32 keeps 32 bits per bound: per column, mantissas scaled to the column's
+ * largest upper bound (resolution ~2^-31 of it), 12 bytes per transition instead
+ * of 20; arithmetic stays 64-bit. See imdp_model_error_bound. */
 typedef enum { IMDP_F64 = 0, IMDP_F32 = 1 } imdp_dtype;
 
 /* Property types of the specification JSON schema (Appendix A). */
@@ -135,6 +138,15 @@ IMDP_API void imdp_model_destroy(imdp_model* m);
 /* Model dimensions and the device bytes it holds. Any output may be NULL. */
 IMDP_API imdp_status imdp_model_info(const imdp_model* m, int32_t* n_states, int32_t* n_cols, int64_t* nnz,
                             size_t* device_bytes, int32_t* max_col_nnz);
+
+/*
+ * A-priori error bound of the model's storage: for IMDP_F32, the largest sum over
+ * one column of |lower - stored lower| + |upper - stored upper|. Values lie in
+ * [0, 1] and the Bellman operator is non-expansive, so K iterations of a
+ * reachability problem on the stored model stay within K * bound of the
+ * binary64 answer (scale by the reward range for rewards). 0 for IMDP_F64.
+ */
+IMDP_API imdp_status imdp_model_error_bound(const imdp_model* m, double* per_iteration);
 
 /*
  * value_iteration / control_synthesis (Sec. 3.2) on one model.

@@ -29,6 +29,7 @@ EXPORTED = [
     "imdp_session_create", "imdp_session_reset", "imdp_session_step", "imdp_session_run", "imdp_session_read",
     "imdp_session_launches", "imdp_session_destroy", "imdp_value_iteration_noalloc",
     "imdp_server_create", "imdp_server_submit", "imdp_server_poll", "imdp_server_wait", "imdp_server_destroy",
+    "imdp_model_error_bound",
 ]
 
 
@@ -106,6 +107,8 @@ def load(path: Optional[str] = None):
     lib.imdp_server_poll.restype = C.c_int
     lib.imdp_server_wait.argtypes = [vp, C.c_uint64, C.c_double, vp, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
     lib.imdp_server_wait.restype = C.c_int
+    lib.imdp_model_error_bound.argtypes = [vp, C.POINTER(C.c_double)]
+    lib.imdp_model_error_bound.restype = C.c_int
     lib.imdp_server_destroy.argtypes = [vp]
     lib.imdp_server_destroy.restype = None
     for f in ("imdp_create_csc", "imdp_create_dense", "imdp_model_info", "imdp_value_iteration",
@@ -174,6 +177,11 @@ class Model:
             self.close()
         except Exception:
             pass
+
+    def error_bound(self) -> float:
+        d = C.c_double(0.0)
+        _check(load().imdp_model_error_bound(C.c_void_p(self.handle), C.byref(d)), "imdp_model_error_bound")
+        return d.value
 
     def info(self):
         ns, nc, nz, mc = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32()

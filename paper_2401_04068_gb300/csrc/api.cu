@@ -147,6 +147,12 @@ imdp_status imdp_model_info(const imdp_model* m, int32_t* n_states, int32_t* n_c
   return IMDP_OK;
 }
 
+imdp_status imdp_model_error_bound(const imdp_model* m, double* per_iteration) {
+  if (!m || !per_iteration) { set_error("NULL argument"); return IMDP_EINVAL; }
+  *per_iteration = m->dev->err_bound;
+  return IMDP_OK;
+}
+
 imdp_status imdp_value_iteration(imdp_model* m, const imdp_spec* spec, double* V_out, int32_t* k_out,
                                  double* residual_out, int32_t* policy_out, void* stream) {
   set_error("");

@@ -82,6 +82,7 @@ struct Stage {
   int32_t sptr[kTileStates + 8];         // stateptr window
   int32_t cptr[kTileCols + 8];           // colptr window
   int32_t hint[kTileCols + 8];           // threshold-hint window
+  int32_t shift[kTileCols + 8];          // per-column shift window (32-bit storage)
   uint8_t fixed[kTileStates + 32];       // reach/avoid mask window
   Problem prob;                          // descriptor of the tile's problem
   Tile tile;                             // set by the producer: the tile in this stage
@@ -100,7 +101,7 @@ struct Smem {
 };
 static_assert(sizeof(int32_t) * (kTileEntries + 8) % 16 == 0, "lg must stay 16-byte aligned");
 static_assert(offsetof(Stage, rem) % 16 == 0 && offsetof(Stage, sptr) % 16 == 0 && offsetof(Stage, cptr) % 16 == 0 &&
-                  offsetof(Stage, fixed) % 16 == 0 && offsetof(Stage, prob) % 16 == 0 && offsetof(Stage, hint) % 16 == 0 && sizeof(Problem) % 16 == 0,
+                  offsetof(Stage, fixed) % 16 == 0 && offsetof(Stage, prob) % 16 == 0 && offsetof(Stage, hint) % 16 == 0 && offsetof(Stage, shift) % 16 == 0 && sizeof(Problem) % 16 == 0,
               "bulk-copy destinations must be 16-byte aligned");
 static_assert(sizeof(Stage) % 16 == 0, "stage alignment");
 static_assert(sizeof(Smem) <= 232448, "shared memory budget of one CTA");
@@ -211,7 +212,23 @@ __device__ __forceinline__ uint64_t warp_excl_scan_sat(uint64_t x, int lane) {
 // through L1). `hint` is the entry that held the threshold in the previous
 // iteration (-1: none); the entry that holds it now is returned in *hint_out.
 // Returns q in Q2.62.
-__device__ uint64_t column_q(const int32_t* rows, const ulonglong2* lg, int32_t k, uint64_t rem,
+// Bounds of one column as {lower, gap} in Q1.63, from 64-bit storage or from
+// 32-bit mantissas shifted up by `down` = 32 - shift_j.
+template <bool f32>
+struct Bounds {
+  const void* p;
+  int down;
+  __device__ __forceinline__ ulonglong2 operator[](int idx) const {
+    if (f32) {
+      const uint2 m = static_cast<const uint2*>(p)[idx];
+      return make_ulonglong2((uint64_t)m.x << down, (uint64_t)m.y << down);
+    }
+    return static_cast<const ulonglong2*>(p)[idx];
+  }
+};
+
+template <bool f32>
+__device__ uint64_t column_q(const int32_t* rows, const Bounds<f32> lg, int32_t k, uint64_t rem,
                              const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane, int32_t hint,
                              int32_t* hint_out) {
   auto key_of = [&](int idx) -> uint64_t {
@@ -483,7 +500,12 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
           const uintptr_t f0 = (uintptr_t)(P.fixed + T.s0), fa = f0 & ~(uintptr_t)15;
           const uintptr_t fe = ((uintptr_t)(P.fixed + T.s1) + 15) & ~(uintptr_t)15;
           st.fixed_off = (int32_t)(f0 - fa);
-          const uint32_t rb = (uint32_t)(ee - eb) * 4u, gb = (uint32_t)(T.e1 - T.e0) * 16u;
+          const uint32_t rb = (uint32_t)(ee - eb) * 4u;
+          // bounds: 16-byte pairs, or (32-bit storage) 8-byte pairs from an aligned
+          // window plus the per-column shift window
+          const int32_t qb = T.e0 & ~1, qe = (T.e1 + 1) & ~1;
+          const uint32_t gb = P.lg32 ? (uint32_t)(qe - qb) * 8u + (uint32_t)(((T.c1 + 4) & ~3) - (T.c0 & ~3)) * 4u
+                                     : (uint32_t)(T.e1 - T.e0) * 16u;
           const uint32_t sbytes = (uint32_t)(se - sb) * 4u, cbytes = (uint32_t)(ce - cb) * 4u;
           const uint32_t mbytes = (uint32_t)(me - mb) * 8u, fbytes = (uint32_t)(fe - fa);
           const uint32_t hbytes = P.hint ? cbytes : 0u;  // same window as colptr
@@ -496,7 +518,13 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
           if (mbytes) bulk_g2s(st.rem, P.rem + mb, mbytes, &S.full[stage]);
           if (fbytes) bulk_g2s(st.fixed, (const void*)fa, fbytes, &S.full[stage]);
           if (rb) bulk_g2s(st.rows, P.rowval + eb, rb, &S.full[stage]);
-          if (gb) bulk_g2s(st.lg, P.lg + T.e0, gb, &S.full[stage]);
+          if (P.lg32) {
+            const uint32_t qbytes = (uint32_t)(qe - qb) * 8u;
+            if (qbytes) bulk_g2s(st.lg, P.lg32 + qb, qbytes, &S.full[stage]);
+            bulk_g2s(st.shift, P.shift + cb, cbytes, &S.full[stage]);
+          } else if (gb) {
+            bulk_g2s(st.lg, P.lg + T.e0, gb, &S.full[stage]);
+          }
           pending_round[stage] = round;
         } else {
           mbar_arrive(&S.full[stage]);  // releases the plain stores above as well
@@ -546,8 +574,16 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
             const int32_t ca = st.cptr[c - cb], ce = st.cptr[c + 1 - cb];
             const int32_t h = P.hint ? st.hint[c - cb] : -1;
             int32_t hout;
-            const uint64_t q = column_q(st.rows + (ca - eb), st.lg + (ca - T.e0), ce - ca, st.rem[c - mb],
-                                        P.V[(k_iter - 1) & 1], P.pessimistic != 0, ws, lane, h, &hout);
+            uint64_t q;
+            if (P.lg32) {
+              const Bounds<true> bd{reinterpret_cast<const uint2*>(st.lg) + (ca - (T.e0 & ~1)), 32 - st.shift[c - cb]};
+              q = column_q<true>(st.rows + (ca - eb), bd, ce - ca, st.rem[c - mb], P.V[(k_iter - 1) & 1],
+                                 P.pessimistic != 0, ws, lane, h, &hout);
+            } else {
+              const Bounds<false> bd{st.lg + (ca - T.e0), 0};
+              q = column_q<false>(st.rows + (ca - eb), bd, ce - ca, st.rem[c - mb], P.V[(k_iter - 1) & 1],
+                                  P.pessimistic != 0, ws, lane, h, &hout);
+            }
             if (lane == 0) {
               st.q[ls] = q;
               if (P.hint && hout != h) P.hint[c] = hout;
@@ -563,8 +599,14 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
               const int32_t ca = __ldg(P.colptr + cc), ce = __ldg(P.colptr + cc + 1);
               const int32_t h = P.hint ? P.hint[cc] : -1;
               int32_t hout;
-              const uint64_t q = column_q(P.rowval + ca, P.lg + ca, ce - ca, __ldg(P.rem + cc), Vin, pess, ws, lane,
-                                          h, &hout);
+              uint64_t q;
+              if (P.lg32) {
+                const Bounds<true> bd{P.lg32 + ca, 32 - __ldg(P.shift + cc)};
+                q = column_q<true>(P.rowval + ca, bd, ce - ca, __ldg(P.rem + cc), Vin, pess, ws, lane, h, &hout);
+              } else {
+                const Bounds<false> bd{P.lg + ca, 0};
+                q = column_q<false>(P.rowval + ca, bd, ce - ca, __ldg(P.rem + cc), Vin, pess, ws, lane, h, &hout);
+              }
               if (lane == 0 && P.hint && hout != h) P.hint[cc] = hout;
               if (best < 0 || (P.maximize ? q > bestq : q < bestq)) {
                 bestq = q;

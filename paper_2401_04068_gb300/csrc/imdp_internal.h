@@ -57,7 +57,10 @@ struct DevModel {
   int32_t* stateptr = nullptr;  // n_states + 1
   int32_t* colptr = nullptr;    // n_cols + 1
   int32_t* rowval = nullptr;    // nnz
-  ulonglong2* lg = nullptr;     // nnz x {lower, gap = upper - lower} in Q1.63
+  ulonglong2* lg = nullptr;     // IMDP_F64: nnz x {lower, gap = upper - lower} in Q1.63
+  uint2* lg32 = nullptr;        // IMDP_F32: nnz x {lower, gap} as 32-bit mantissas, value = m * 2^-(31 + shift_j)
+  int32_t* shift = nullptr;     // IMDP_F32: per-column shift_j (padded like colptr)
+  double err_bound = 0.0;       // IMDP_F32: max over columns of sum |dlower| + |dupper| (per-iteration error bound)
   uint64_t* rem = nullptr;      // n_cols: 1 - sum(lower) in Q1.63 (clamped at 0)
   size_t bytes = 0;
   std::vector<int32_t> h_stateptr;  // host copies of the structure (tile planning)
@@ -76,6 +79,8 @@ struct alignas(16) Problem {
   const int32_t* rowval;
   const ulonglong2* lg;
   const uint64_t* rem;
+  const uint2* lg32;      // 32-bit storage (nullptr for 64-bit models)
+  const int32_t* shift;   // per-column shift of the 32-bit storage
   const uint8_t* fixed;   // n_states: 0 free, 1 held at 1 (reach target), 2 held at 0 (avoid)
   uint64_t* V[2];         // ping-pong value buffers; iteration k writes V[k & 1]
   int32_t* policy;        // nullable; see policy_mode

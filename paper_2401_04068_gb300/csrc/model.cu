@@ -67,6 +67,61 @@ __global__ void convert_columns_kernel(int32_t n_states, int32_t n_cols, const i
   }
 }
 
+// 32-bit storage: per column, shift s = the largest value with max(upper) <
+// 2^(64 - s) in Q1.63, so every bound is m * 2^(32 - s) in Q1.63 with m < 2^32
+// (resolution 2^-(31 + s) in probability, i.e. ~2^-31 of the column's largest
+// bound). Lower and upper are rounded to nearest, the gap is their difference,
+// rem is recomputed exactly from the rounded lower bounds, and the column's
+// total rounding error sum |dlower| + |dupper| is reported.
+__global__ void quantize_columns_kernel(int32_t n_cols, const int32_t* __restrict__ colptr,
+                                        const ulonglong2* __restrict__ lg, uint2* __restrict__ lg32,
+                                        int32_t* __restrict__ shift, uint64_t* __restrict__ rem,
+                                        double* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (int32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n_cols; j += warps) {
+    const int32_t a = colptr[j], b = colptr[j + 1];
+    unsigned long long umax = 0;
+    for (int32_t i = a + lane; i < b; i += 32) {
+      const unsigned long long u = lg[i].x + lg[i].y;
+      umax = u > umax ? u : umax;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, umax, o);
+      umax = t > umax ? t : umax;
+    }
+    const int bl = umax ? 64 - __clzll((long long)umax) : 1;  // bit length of the largest bound
+    int sh = 64 - bl;                                          // umax < 2^(64 - sh)
+    sh = sh > 31 ? 31 : sh;
+    const int down = 32 - sh;                                  // Q1.63 = m << down
+    const unsigned long long half = 1ull << (down - 1);
+    unsigned long long lsum = 0;
+    double e = 0.0;
+    for (int32_t i = a + lane; i < b; i += 32) {
+      const unsigned long long L = lg[i].x, U = lg[i].x + lg[i].y;
+      unsigned long long mL = (L >> down) + (((L & ((1ull << down) - 1)) >= half) ? 1ull : 0ull);
+      unsigned long long mU = (U >> down) + (((U & ((1ull << down) - 1)) >= half) ? 1ull : 0ull);
+      mL = mL > 0xffffffffull ? 0xffffffffull : mL;
+      mU = mU > 0xffffffffull ? 0xffffffffull : mU;
+      lg32[i] = make_uint2((unsigned)mL, (unsigned)(mU - mL));
+      const unsigned long long Lq = mL << down, Uq = mU << down;
+      lsum += Lq;
+      e += (double)(Lq > L ? Lq - L : L - Lq) + (double)(Uq > U ? Uq - U : U - Uq);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+    }
+    if (lane == 0) {
+      shift[j] = sh;
+      rem[j] = lsum >= kOne ? 0ull : kOne - lsum;
+      err[j] = e / 9223372036854775808.0;
+    }
+  }
+}
+
 struct DevBuf {
   void* p = nullptr;
   ~DevBuf() {
@@ -84,6 +139,8 @@ void model_destroy(DevModel* m) {
   cudaFree(m->lg);
   cudaFree(m->rem);
   cudaFree(m->tiles);
+  cudaFree(m->lg32);
+  cudaFree(m->shift);
   delete m;
 }
 
@@ -100,8 +157,8 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
     set_error("NULL array");
     return IMDP_EINVAL;
   }
-  if (dtype != IMDP_F64) {
-    set_error("only IMDP_F64 storage is supported by this build");
+  if (dtype != IMDP_F64 && dtype != IMDP_F32) {
+    set_error("dtype must be IMDP_F64 or IMDP_F32");
     return IMDP_EINVAL;
   }
   // Structure arrays are small (states + columns): check them on the host.
@@ -196,6 +253,35 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
     model_destroy(m);
     set_error("infeasible column: need 0 <= lower <= upper <= 1 and sum lower <= 1 <= sum upper (tol 1e-12)");
     return IMDP_EINFEASIBLE;
+  }
+  if (dtype == IMDP_F32) {
+    // re-encode the bounds in 32 bits and drop the 64-bit copy
+    const size_t nz32 = ((nz + 1) & ~size_t(1)) + 2;  // padded for 16-byte bulk-copy windows
+    DevBuf derr2;
+    if (cudaMalloc(&m->lg32, sizeof(uint2) * nz32) != cudaSuccess ||
+        cudaMalloc(&m->shift, sizeof(int32_t) * nc_pad) != cudaSuccess ||
+        cudaMalloc(&derr2.p, sizeof(double) * n_cols) != cudaSuccess) {
+      cudaGetLastError();
+      model_destroy(m);
+      set_error("device allocation failed for 32-bit storage");
+      return IMDP_ENOMEM;
+    }
+    e = cudaMemsetAsync(m->lg32, 0, sizeof(uint2) * nz32, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->shift, 0, sizeof(int32_t) * nc_pad, st);
+    if (e == cudaSuccess) {
+      quantize_columns_kernel<<<grid, 256, 0, st>>>(n_cols, m->colptr, m->lg, m->lg32, m->shift, m->rem,
+                                                    (double*)derr2.p);
+      e = cudaGetLastError();
+    }
+    std::vector<double> herrs(n_cols);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(herrs.data(), derr2.p, sizeof(double) * n_cols, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { model_destroy(m); return cuda_status(e, "32-bit storage"); }
+    for (double x : herrs) m->err_bound = std::max(m->err_bound, x);
+    cudaFree(m->lg);
+    m->lg = nullptr;
+    m->bytes = m->bytes - sizeof(ulonglong2) * nz + sizeof(uint2) * nz32 + sizeof(int32_t) * nc_pad;
   }
   m->h_stateptr = std::move(hs);
   m->h_colptr = std::move(hc);

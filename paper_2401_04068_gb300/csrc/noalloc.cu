@@ -143,6 +143,8 @@ extern "C" IMDP_API imdp_status imdp_value_iteration_noalloc(imdp_model* m, cons
   P.rowval = dm->rowval;
   P.lg = dm->lg;
   P.rem = dm->rem;
+  P.lg32 = dm->lg32;
+  P.shift = dm->shift;
   P.fixed = d_mask;
   P.V[0] = d_V;
   P.V[1] = d_V + n;

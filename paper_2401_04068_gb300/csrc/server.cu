@@ -183,6 +183,8 @@ struct Server {
     P.rowval = m->rowval;
     P.lg = m->lg;
     P.rem = m->rem;
+    P.lg32 = m->lg32;
+    P.shift = m->shift;
     P.fixed = mask;
     P.V[0] = V;
     P.V[1] = V + n;

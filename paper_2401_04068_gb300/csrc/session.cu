@@ -190,6 +190,8 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
     P.rowval = m->rowval;
     P.lg = m->lg;
     P.rem = m->rem;
+    P.lg32 = m->lg32;
+    P.shift = m->shift;
     P.fixed = S->fixed + S->base_h[p];
     P.hint = S->hints + col_off;
     col_off += (int64_t)padded_i32(m->n_cols);

@@ -332,3 +332,61 @@ def test_session_reset_restarts_from_v0():
     np.testing.assert_array_equal(V1, V2)
     _, oV, _, _, _ = run_oracle(m, horizon=40, reach=m.goal)
     np.testing.assert_allclose(V2, oV, atol=TOL_F64)
+
+
+# --------------------------------------------------------------------------- 32-bit storage
+
+@pytest.mark.parametrize("pess,maxi", MODES)
+def test_f32_storage_within_a_priori_bound(pess, maxi):
+    m = banded_imdp(400, 3, 400 * 3 * 40 + 1, eps=0.1, seed=70)
+    model = g.create_model(m, dtype=g.IMDP_F32)
+    d = model.error_bound()
+    assert 0.0 < d < 1e-8
+    K = 60
+    st, V, k, res, _ = g.value_iteration(model, m.n_states, horizon=K, reach=m.goal, pessimistic=pess, maximize=maxi)
+    _, oV, _, _, _ = run_oracle(m, horizon=K, reach=m.goal, pessimistic=pess, maximize=maxi)
+    err = float(np.max(np.abs(V - oV)))
+    assert err <= K * d + 1e-10, (err, K * d)
+
+
+@pytest.mark.parametrize("name", ["pendulum240_x4096", "pimdp2"])
+def test_f32_storage_benchmark_shapes_1e6(name):
+    # the benchmark query (K = 200) on the 32-bit path stays within 1e-6 of the
+    # binary64 oracle (checked on the oracle-sized part of each workload)
+    if name == "pendulum240_x4096":
+        m = make_config(name, n_models=16)
+    else:
+        m = make_config(name)
+    model = g.create_model(m, dtype=g.IMDP_F32)
+    K = 200
+    st, V, k, res, _ = g.value_iteration(model, m.n_states, horizon=K, reach=m.goal)
+    assert k == K and model.error_bound() * K < 1e-5
+    if name == "pimdp2":
+        # full-size: the last step recomputed by the oracle from the GPU's V_{K-1}
+        # on the stored (rounded) bounds is within rounding; against binary64 bounds
+        # the per-iteration bound applies
+        Vprev = V - res
+        rng = np.random.default_rng(1)
+        for s in rng.choice(m.n_states, 48, replace=False):
+            if s in set(m.goal.tolist()):
+                continue
+            qs = []
+            for j in range(m.stateptr[s], m.stateptr[s + 1]):
+                a, b = m.colptr[j], m.colptr[j + 1]
+                qs.append(oracle.omax_column(Vprev[m.rowval[a:b]], m.lower[a:b], m.upper[a:b], True)[0])
+            assert abs(V[s] - max(qs)) <= model.error_bound() + 1e-12
+    else:
+        _, oV, _, _, _ = run_oracle(m, horizon=K, reach=m.goal)
+        assert float(np.max(np.abs(V - oV))) <= 1e-6
+
+
+def test_f32_batch_with_f64_models():
+    ms = [banded_imdp(200, 2, 200 * 2 * 15 + 1, seed=71), banded_imdp(100, 1, 100 * 30 + 1, seed=72)]
+    models = [g.create_model(ms[0], dtype=g.IMDP_F32), g.create_model(ms[1])]
+    specs = [g.make_spec(horizon=30, reach=ms[0].goal), g.make_spec(horizon=20, reach=ms[1].goal)]
+    outs = [np.zeros(ms[0].n_states), np.zeros(ms[1].n_states)]
+    g.imdp_value_iteration_batch(models, specs, outs)
+    _, o0, _, _, _ = run_oracle(ms[0], horizon=30, reach=ms[0].goal)
+    _, o1, _, _, _ = run_oracle(ms[1], horizon=20, reach=ms[1].goal)
+    assert np.max(np.abs(outs[0] - o0)) <= 30 * models[0].error_bound() + 1e-10
+    np.testing.assert_allclose(outs[1], o1, atol=TOL_F64)
