@@ -7,8 +7,10 @@
 // state-aligned tiles (consecutive states of one problem, <= kTileEntries
 // entries). A producer warp streams each tile's destination indices and bound
 // pairs into a three-stage shared-memory ring with bulk asynchronous copies
-// (cp.async.bulk, completion counted on an mbarrier), while twelve consumer warps
-// work on the tiles already landed. Every entry crosses HBM once per iteration.
+// (cp.async.bulk, completion counted on an mbarrier), while fifteen consumer
+// warps work on the tiles already landed (16 warps: four per SM sub-partition,
+// which leaves 128 registers per thread). Every entry crosses HBM once per
+// iteration.
 //
 // O-maximization without a sort. For a pessimistic adversary the procedure of
 // Sec. 4 orders the destinations by ascending V, starts from p = lower and hands
@@ -22,8 +24,11 @@
 //     v* = the smallest V_i with sum_{V_j <= V_i} gap_j >= rem.
 // Keys are the Q1.63 values (complemented for an optimistic adversary so that the
 // order is always ascending). A consumer warp handles one column at a time:
-//   1. gathers V for the column, stores the keys in shared memory and takes the
-//      min/max key (redux.sync on 32-bit halves);
+//   0. warm start: the entry that held the threshold in the previous iteration is
+//      tried first; one pass over the column checks F(<v) < rem <= F(<=v) exactly
+//      and, when it holds (the usual case once V settles), yields q directly;
+//   1. otherwise it gathers the keys and takes their min/max (redux.sync on
+//      32-bit halves);
 //   2. histograms the gaps (and counts) into 64 bins of [min, max] and scans the
 //      bins: the bin where the prefix crosses rem holds the threshold, entries in
 //      lower bins are fully "below";
@@ -32,10 +37,10 @@
 //      entries before it in (key, position) order leave of rem.
 // A crossing bin with more than 32 entries is narrowed by further rounds over its
 // key range; a bin whose entries share one key is resolved as a group. Sums are
-// exact 64-bit integer sums, so results do not depend on the order in which lanes
-// or bins are combined. After all columns of a tile, the consumer threads take
-// the optimum over each state's actions, apply the reach/avoid mask and write V,
-// the policy and the residual.
+// exact 64-bit integer sums (gap sums saturate instead of wrapping), so results
+// do not depend on the order in which lanes or bins are combined. The warp that
+// finishes a tile's last column takes the optimum over each state's actions,
+// applies the reach/avoid mask and writes V, the policy and the residual.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,7 +54,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBins = 64;
-constexpr int kConsumerWarps = 16;
+constexpr int kConsumerWarps = 15;
 constexpr int kStages = 3;
 constexpr int kBlockThreads = 32 * (kConsumerWarps + 1);
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz: bound of every wait
@@ -255,17 +260,25 @@ __device__ uint64_t column_q(const int32_t* rows, const Bounds<f32> lg, int32_t 
   if (hint >= 0 && hint < k) {
     const uint64_t vk = __ldg(V + rows[hint]);
     uint64_t acc = 0, flt = 0, geq = 0;
+    uint32_t fc = 0, gc = 0;
+    // warp-uniform trip count; padding entries read row 0 and contribute zero
+    const int nb = (k + 31) >> 5;
 #pragma unroll 4
-    for (int idx = lane; idx < k; idx += 32) {
-      const uint64_t v = __ldg(V + rows[idx]);
-      const ulonglong2 b = lg[idx];
+    for (int it = 0; it < nb; ++it) {
+      const int idx = it * 32 + lane;
+      const bool ok = idx < k;
+      const uint64_t v = __ldg(V + (ok ? rows[idx] : 0));
+      const ulonglong2 b = ok ? lg[idx] : make_ulonglong2(0, 0);
       const bool below = pess ? (v < vk) : (v > vk);
-      acc += __umul64hi(v, below ? b.x + b.y : b.x);
-      if (below) flt = sat_add(flt, b.y);
-      if (v == vk) geq = sat_add(geq, b.y);
+      acc += __umul64hi(v, b.x + (below ? b.y : 0ull));
+      const uint64_t gb = below ? b.y : 0ull, ge = v == vk ? b.y : 0ull;
+      flt += gb;
+      fc += flt < gb ? 1u : 0u;
+      geq += ge;
+      gc += geq < ge ? 1u : 0u;
     }
-    flt = warp_sum_sat(flt);
-    geq = warp_sum_sat(geq);
+    flt = warp_sum_sat(fc ? ~0ull : flt);
+    geq = warp_sum_sat(gc ? ~0ull : geq);
     if (flt < rem && rem - flt <= geq) {
       *hint_out = hint;
       return warp_sum_u64(acc) + __umul64hi(vk, rem - flt);
@@ -274,11 +287,15 @@ __device__ uint64_t column_q(const int32_t* rows, const Bounds<f32> lg, int32_t 
 
   // 2. key range
   uint64_t lmin = ~0ull, lmax = 0;
+  const int nb = (k + 31) >> 5;
 #pragma unroll 4
-  for (int idx = lane; idx < k; idx += 32) {
-    const uint64_t key = key_of(idx);
-    lmin = key < lmin ? key : lmin;
-    lmax = key > lmax ? key : lmax;
+  for (int it = 0; it < nb; ++it) {
+    const int idx = it * 32 + lane;
+    if (idx < k) {
+      const uint64_t key = key_of(idx);
+      lmin = key < lmin ? key : lmin;
+      lmax = key > lmax ? key : lmax;
+    }
   }
   // 3. threshold search: after it, keys < lo are below (full gap), keys > hi are
   // above (lower bound), keys in [lo, hi] are candidates sharing rem - fb.

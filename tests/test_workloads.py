@@ -47,3 +47,33 @@ def test_concat():
 def test_config_table_covers_paper_rows():
     assert {"linear5", "pendulum240_x4096", "cartpole3840", "harrier", "pimdp2"} <= set(CONFIGS)
     assert CONFIGS["pimdp2"]["nnz"] == 48106480 and CONFIGS["harrier"]["nnz"] == 18574307
+
+
+def test_uneven_batch_shapes_valid_and_thread_independent():
+    from workloads.imdp_synth import uneven_batch
+    a, Ka = uneven_batch(40, seed=3, threads=1)
+    b, Kb = uneven_batch(40, seed=3, threads=4)
+    assert np.array_equal(Ka, Kb) and Ka.min() >= 50 and Ka.max() <= 500
+    for x, y in zip(a, b):
+        for f in ("stateptr", "colptr", "rowval", "lower", "upper", "goal"):
+            assert np.array_equal(getattr(x, f), getattr(y, f))
+        assert 6 <= x.n_states <= 961
+        acts = np.diff(x.stateptr)
+        assert 1 <= acts[:-1].min() and acts.max() <= 4 and acts[-1] == 1
+        assert x.colptr[-1] == x.nnz and x.rowval.min() >= 0 and x.rowval.max() < x.n_states
+        assert x.goal.min() >= 0 and x.goal.max() < x.n_states - 1
+        assert oracle.validate(oracle.OracleIMDP(x.n_states, x.stateptr, x.colptr, x.rowval, x.lower,
+                                                 x.upper)) == "ok"
+
+
+def test_served_stream_requests_refer_to_earlier_models():
+    from workloads.imdp_synth import served_stream
+    models, reqs = served_stream(60, seed=2)
+    seen = -1
+    for (mi, K, pess, goal) in reqs:
+        assert mi <= seen + 1
+        seen = max(seen, mi)
+        assert 100 <= K <= 500
+        n = models[mi].n_states
+        assert 50 <= n <= 4000 and goal.min() >= 0 and goal.max() < n - 1
+    assert seen + 1 == len(models)

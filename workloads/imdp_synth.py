@@ -89,24 +89,32 @@ def _split_total(rng, total: int, parts: int, spread: float, lo: int, hi: int) -
     return k
 
 
-def _banded_core(rng, n_models: int, n_domain: int, n_actions: int, kk: np.ndarray, eps: np.ndarray,
+def _banded_core(rng, n_models: int, n_domain, n_actions, kk: np.ndarray, eps: np.ndarray,
                  goal_frac: float = 0.1):
-    """Vectorised generator for ``n_models`` models of identical shape.
+    """Vectorised generator for ``n_models`` models.
 
-    kk: in-domain window length per column (n_models * n_domain * n_actions), eps per model.
-    Returns the concatenated block-diagonal CSC arrays."""
-    n_states_m = n_domain + 1
-    m_cols_m = n_domain * n_actions + 1
-    N = n_models * n_domain * n_actions
-    model = np.repeat(np.arange(n_models), n_domain * n_actions)
-    state = np.tile(np.repeat(np.arange(n_domain), n_actions), n_models)
-    action = np.tile(np.arange(n_actions), n_models * n_domain)
+    n_domain, n_actions: scalars (all models alike) or one value per model;
+    kk: in-domain window length per grid column (models in order, then states,
+    then actions); eps: one value per model.  Returns the concatenated
+    block-diagonal CSC arrays."""
+    nd = np.broadcast_to(np.asarray(n_domain, dtype=np.int64), (n_models,))
+    na = np.broadcast_to(np.asarray(n_actions, dtype=np.int64), (n_models,))
+    cols_m = nd * na
+    colbase = np.zeros(n_models + 1, dtype=np.int64)
+    np.cumsum(cols_m, out=colbase[1:])
+    N = int(colbase[-1])
+    model = np.repeat(np.arange(n_models), cols_m)
+    local = np.arange(N) - colbase[model]
+    na_c = na[model]
+    nd_c = nd[model]
+    state = local // na_c
+    action = local % na_c
     kk = np.asarray(kk, dtype=np.int64)
     sigma = np.maximum(kk / 4.0, 0.5)
     # actions shift the kernel left/centre/right; jitter keeps columns distinct
-    drift = (action - (n_actions - 1) / 2.0) * np.maximum(kk / 3.0, 1.0)
+    drift = (action - (na_c - 1) / 2.0) * np.maximum(kk / 3.0, 1.0)
     centre = state + drift + rng.normal(0.0, 0.25, N) * sigma
-    start = np.clip(np.round(centre - kk / 2.0).astype(np.int64), 0, n_domain - kk)
+    start = np.clip(np.round(centre - kk / 2.0).astype(np.int64), 0, nd_c - kk)
     # entries per column: window + sink
     cnt = kk + 1
     colstart = np.zeros(N + 1, dtype=np.int64)
@@ -119,7 +127,7 @@ def _banded_core(rng, n_models: int, n_domain: int, n_actions: int, kk: np.ndarr
     w = np.exp(-0.5 * ((dest - centre[col_of]) / sigma[col_of]) ** 2)
     w[is_sink] = 0.0
     wsum = np.add.reduceat(w, colstart[:-1])
-    dist = np.minimum(centre, (n_domain - 1) - centre)
+    dist = np.minimum(centre, (nd_c - 1) - centre)
     leak = 1e-3 + 0.3 * np.exp(-np.maximum(dist, 0.0) / sigma)
     p = np.where(is_sink, leak[col_of], w / wsum[col_of] * (1.0 - leak[col_of]))
     u1 = rng.random(tot)
@@ -128,39 +136,43 @@ def _banded_core(rng, n_models: int, n_domain: int, n_actions: int, kk: np.ndarr
     lower = p * (1.0 - e * u1)
     upper = np.minimum(1.0, p * (1.0 + e * u2))
     # local -> global destination indices; the sink is the last state of each model
-    base = model[col_of] * n_states_m
-    rowval = np.where(is_sink, base + n_domain, base + dest).astype(np.int32)
+    sbase = np.zeros(n_models + 1, dtype=np.int64)
+    np.cumsum(nd + 1, out=sbase[1:])
+    base = sbase[model][col_of]
+    rowval = np.where(is_sink, base + nd_c[col_of], base + dest).astype(np.int32)
 
     # insert each model's sink column (self-loop, lower = upper = 1)
-    per_model_entries = np.add.reduceat(cnt, np.arange(0, N, n_domain * n_actions))
-    ins_at = np.cumsum(per_model_entries)  # positions (before insertion) at model ends
-    rowval = np.insert(rowval, ins_at, (np.arange(n_models) * n_states_m + n_domain).astype(np.int32))
+    ins_at = colstart[colbase[1:]]  # positions (before insertion) at model ends
+    sinks = sbase[:-1] + nd
+    rowval = np.insert(rowval, ins_at, sinks.astype(np.int32))
     lower = np.insert(lower, ins_at, 1.0)
     upper = np.insert(upper, ins_at, 1.0)
-    cnt_all = np.insert(cnt.reshape(n_models, -1), n_domain * n_actions, 1, axis=1).reshape(-1)
+    cnt_all = np.insert(cnt, colbase[1:], 1)
     colptr = np.zeros(cnt_all.size + 1, dtype=np.int64)
     np.cumsum(cnt_all, out=colptr[1:])
-    acts = np.full(n_models * n_states_m, n_actions, dtype=np.int64)
-    acts[n_domain::n_states_m] = 1
+    acts = np.repeat(na, nd + 1)
+    acts[sinks] = 1
     stateptr = np.zeros(acts.size + 1, dtype=np.int64)
     np.cumsum(acts, out=stateptr[1:])
     # target block in the middle of each model's domain
-    g = max(1, int(round(goal_frac * n_domain)))
-    g0 = (n_domain - g) // 2
-    goal = (np.arange(n_models)[:, None] * n_states_m + g0 + np.arange(g)[None, :]).reshape(-1)
-    sink = np.arange(n_models) * n_states_m + n_domain
+    g = np.maximum(1, np.round(goal_frac * nd).astype(np.int64))
+    g0 = (nd - g) // 2
+    gbase = np.zeros(n_models + 1, dtype=np.int64)
+    np.cumsum(g, out=gbase[1:])
+    gm = np.repeat(np.arange(n_models), g)
+    goal = sbase[gm] + g0[gm] + (np.arange(int(gbase[-1])) - gbase[gm])
     if colptr[-1] >= 2**31:
         raise ValueError("model too large for int32 column pointers")
     return IMDPInput(
-        n_states=n_models * n_states_m,
+        n_states=int(sbase[-1]),
         stateptr=stateptr.astype(np.int32),
         colptr=colptr.astype(np.int32),
         rowval=rowval,
         lower=lower,
         upper=upper,
         goal=goal.astype(np.int32),
-        sink=sink.astype(np.int32),
-        model_state_offsets=(np.arange(n_models + 1) * n_states_m).astype(np.int64),
+        sink=sinks.astype(np.int32),
+        model_state_offsets=sbase,
     )
 
 
@@ -196,6 +208,112 @@ def banded_batch(n_models: int, n_domain: int, n_actions: int, nnz_per_model: in
     if stress_frac > 0:
         eps_m[rng.random(n_models) < stress_frac] = stress_eps
     return _banded_core(rng, n_models, n_domain, n_actions, kk, eps_m, goal_frac)
+
+
+def _split_models(big: IMDPInput, n_models: int) -> List[IMDPInput]:
+    """Cut a block-diagonal IMDP into its independent models (local indices)."""
+    out = []
+    sb = big.model_state_offsets
+    gi = np.searchsorted(big.goal, sb)
+    for i in range(n_models):
+        s0, s1 = int(sb[i]), int(sb[i + 1])
+        c0, c1 = int(big.stateptr[s0]), int(big.stateptr[s1])
+        e0, e1 = int(big.colptr[c0]), int(big.colptr[c1])
+        out.append(IMDPInput(
+            n_states=s1 - s0,
+            stateptr=(big.stateptr[s0:s1 + 1] - c0).astype(np.int32),
+            colptr=(big.colptr[c0:c1 + 1] - e0).astype(np.int32),
+            rowval=(big.rowval[e0:e1] - s0).astype(np.int32),
+            lower=big.lower[e0:e1].copy(),
+            upper=big.upper[e0:e1].copy(),
+            goal=(big.goal[gi[i]:gi[i + 1]] - s0).astype(np.int32),
+            sink=np.array([s1 - 1 - s0], np.int32),
+            model_state_offsets=np.array([0, s1 - s0], np.int64),
+        ))
+    return out
+
+
+def shaped_models(n_domain: np.ndarray, n_actions: np.ndarray, kbar: np.ndarray, eps: np.ndarray,
+                  seed: int = 0, chunk: int = 128, threads: int = 0) -> List[IMDPInput]:
+    """Independent banded models of per-model shape: ``n_domain[i] + 1`` states,
+    ``n_actions[i]`` actions, in-domain windows of about ``kbar[i]`` entries
+    (each column's length drawn uniformly within +-50 % of it, clipped to
+    [1, n_domain[i]]).  Models are generated in chunks of ``chunk`` with one
+    PCG64 stream per chunk (spawned from ``seed``), so the result does not
+    depend on ``threads``; numpy releases the GIL in the array work, so a
+    thread pool shortens generation of large sets."""
+    n = len(n_domain)
+    nd = np.asarray(n_domain, np.int64)
+    na = np.asarray(n_actions, np.int64)
+    kb = np.asarray(kbar, np.float64)
+    ep = np.asarray(eps, np.float64)
+    bounds = list(range(0, n, chunk)) + [n]
+    seqs = np.random.SeedSequence(seed).spawn(len(bounds) - 1)
+
+    def one(ci):
+        a, b = bounds[ci], bounds[ci + 1]
+        rng = np.random.Generator(np.random.PCG64(seqs[ci]))
+        cols = nd[a:b] * na[a:b]
+        kc = np.repeat(kb[a:b], cols) * (1.0 + 0.5 * (rng.random(int(cols.sum())) * 2.0 - 1.0))
+        kk = np.clip(np.round(kc).astype(np.int64), 1, np.repeat(nd[a:b], cols))
+        big = _banded_core(rng, b - a, nd[a:b], na[a:b], kk, ep[a:b])
+        return _split_models(big, b - a)
+
+    nchunks = len(bounds) - 1
+    if threads and threads > 1 and nchunks > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            parts = list(ex.map(one, range(nchunks)))
+    else:
+        parts = [one(ci) for ci in range(nchunks)]
+    return [m for part in parts for m in part]
+
+
+def uneven_batch(n_models: int = 10000, seed: int = 7, threads: int = 0):
+    """Heterogeneous batch: states ~ U{6..961}, actions ~ U{1..4}, mean
+    in-domain window ~ U{2..min(400, states - 1)}, eps in {0.05, 0.1} and
+    horizon K ~ U{50..500} per problem (the spread of the table's rows from
+    linear_5 to cartpole_960).  Returns (models, horizons)."""
+    rng = _rng(seed)
+    states = rng.integers(6, 962, n_models)
+    nd = states - 1
+    na = rng.integers(1, 5, n_models)
+    kbar = rng.integers(2, np.minimum(400, nd) + 1)
+    eps = rng.choice([0.05, 0.1], n_models)
+    horizons = rng.integers(50, 501, n_models).astype(np.int32)
+    return shaped_models(nd, na, kbar, eps, seed=seed + 1, threads=threads), horizons
+
+
+def served_stream(n_requests: int, seed: int = 8, repeat_frac: float = 0.3, threads: int = 0):
+    """Request stream for serving: states ~ log-U[50, 4000], actions ~ U{1..3},
+    mean window ~ log-U[3, 700] (capped at the domain), K ~ U{100..500}; a
+    fraction ``repeat_frac`` of requests re-query an earlier request's model
+    with another target block and adversary.  Returns (models, requests) with
+    requests as tuples (model index, horizon, pessimistic, goal)."""
+    rng = _rng(seed)
+    is_new = rng.random(n_requests) >= repeat_frac
+    is_new[0] = True
+    n_new = int(is_new.sum())
+    states = np.exp(rng.uniform(np.log(50), np.log(4000), n_new)).astype(np.int64)
+    nd = states - 1
+    na = rng.integers(1, 4, n_new)
+    kbar = np.minimum(np.exp(rng.uniform(np.log(3), np.log(700), n_new)), nd)
+    eps = rng.choice([0.05, 0.1], n_new)
+    models = shaped_models(nd, na, kbar, eps, seed=seed + 1, threads=threads)
+    reqs = []
+    j = -1
+    for i in range(n_requests):
+        K = int(rng.integers(100, 501))
+        if is_new[i]:
+            j += 1
+            reqs.append((j, K, True, models[j].goal))
+        else:
+            mi = int(rng.integers(0, j + 1))
+            n = models[mi].n_states - 1
+            g = max(1, n // 10)
+            g0 = int(rng.integers(0, n - g + 1))
+            reqs.append((mi, K, bool(rng.random() < 0.5), np.arange(g0, g0 + g, dtype=np.int32)))
+    return models, reqs
 
 
 def random_imdp(n_states: int, max_actions: int = 3, density: float = 0.6, seed: int = 0,
