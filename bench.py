@@ -355,6 +355,174 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(out), flush=True)
 
 
+def _gpu_setup(rank, world, local_rank):
+    import torch
+    import paper_2401_04068_gb300 as g
+    from paper_2401_04068_gb300 import build as pbuild
+    torch.cuda.set_device(local_rank)
+    if not os.path.exists(pbuild.LIB) or not pbuild.up_to_date():
+        if rank == 0 or world == 1:
+            pbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    g.load()
+    return torch.device("cuda", local_rank)
+
+
+def run_uneven(args, rank, world, local_rank):
+    """Heterogeneous batch: 10,000 problems of different shapes and horizons in one
+    resident session; a step runs every problem to its own horizon."""
+    import torch
+    import paper_2401_04068_gb300 as g
+    from workloads.imdp_synth import uneven_batch
+    dev = _gpu_setup(rank, world, local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    n = args.models or 10000
+    t = time.perf_counter()
+    ms, Ks = uneven_batch(n, seed=7 + 1000 * rank, threads=os.cpu_count() or 1)
+    gen_s = time.perf_counter() - t
+    dtype = g.IMDP_F32 if args.dtype == "f32" else g.IMDP_F64
+    models = [g.create_model(m, dtype=dtype, stream=stream) for m in ms]
+    specs = [g.make_spec(horizon=int(K), reach=m.goal, pessimistic=True, maximize=True) for m, K in zip(ms, Ks)]
+    sess = g.imdp_session_create(models, specs, stream=stream)
+    kmax = int(Ks.max())
+
+    def one_step(ev=None):
+        g.imdp_session_reset(sess, stream)
+        if ev is not None:
+            ev[0].record(stream)
+        g.imdp_session_step(sess, kmax, stream)
+        if ev is not None:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    for i in (0, n // 2, n - 1):  # every problem stops at its own horizon
+        kk = [0]
+        Vd = torch.empty(ms[i].n_states, dtype=torch.float64, device=dev)
+        g.imdp_session_read(sess, i, Vd, kk, stream=stream)
+        assert kk[0] == int(Ks[i]), (i, kk[0], int(Ks[i]))
+    launches0 = g.imdp_session_launches(sess)
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0.record(stream)
+    for i in range(args.steps):
+        one_step(kev[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    kernel_ms = sum(a.elapsed_time(b) for a, b in kev)
+    launches = g.imdp_session_launches(sess) - launches0
+    nnz = np.array([m.nnz for m in ms], np.float64)
+    my_units = float((nnz * Ks).sum()) * args.steps
+    elapsed_ms, kernel_ms, total_units = reduce_across_ranks(elapsed_ms, kernel_ms, my_units, world, dev)
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peak_hbm()
+    alg = sum(algorithmic_bytes_per_iteration(m, args.dtype) * int(K) for m, K in zip(ms, Ks))
+    achieved = alg * args.steps / (kernel_ms / 1e3) / 1e9
+    out = {
+        "metric": METRIC.replace("K=200", "K per problem"), "value": total_units / (elapsed_ms / 1e3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded banded IMDPs, per-problem shapes and horizons)",
+        "config": {"workload": f"uneven_x{n}", "problems": n, "transitions": int(nnz.sum()),
+                   "states": int(sum(m.n_states for m in ms)), "horizon": "U{50..500} per problem",
+                   "max_horizon": kmax, "shapes": "states U{6..961}, actions U{1..4}, window U{2..min(400,n)}",
+                   "l2": "inputs larger than L2 (%.1f GB resident)" % (nnz.sum() * 20 / 1e9),
+                   "generation_s": round(gen_s, 1), "parallelism": "replicas"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind, "kernel": "bellman_step_kernel",
+                     "note": "algorithmic bytes of every running problem summed over the step's launches"},
+        "clocks": clk, "gpu_launches": int(launches + args.steps), "e2e": None,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_served(args, rank, world, local_rank):
+    """Continuous-batching server under a Poisson request stream: requests arrive at
+    `--rate` per second; 70 % bring a new model (created on arrival, inside the
+    measured latency), 30 % re-query a resident one. Latency = arrival to result."""
+    import queue as _queue
+    import torch
+    import paper_2401_04068_gb300 as g
+    from workloads.imdp_synth import served_stream
+    dev = _gpu_setup(rank, world, local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    n_req = args.requests
+    models_h, reqs = served_stream(n_req, seed=8 + 1000 * rank, threads=os.cpu_count() or 1)
+    server = g.imdp_server_create(int(args.server_budget_gb * (1 << 30)))
+    # warm-up: one request through the whole path (module load, first graph)
+    w = g.create_model(models_h[0], stream=stream)
+    tk = g.imdp_server_submit(server, w, g.make_spec(horizon=10, reach=models_h[0].goal))
+    assert g.imdp_server_wait(server, tk, 60000.0, np.zeros(models_h[0].n_states)) == g.IMDP_OK
+    rng = np.random.default_rng(99 + rank)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
+    dev_models = [None] * len(models_h)
+    done = [None] * n_req
+    q = _queue.Queue()
+
+    def waiter():
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            i, tk, t_sub, n = item
+            V = np.zeros(n)
+            k = [0]
+            lat = [0.0]
+            st = g.imdp_server_wait(server, tk, 600000.0, V, k, lat)
+            done[i] = (st, k[0], t_sub + lat[0] / 1e3)
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t0 = time.perf_counter()
+    for i, (mi, K, pess, goal) in enumerate(reqs):
+        delay = t0 + arrivals[i] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        if dev_models[mi] is None:
+            dev_models[mi] = g.create_model(models_h[mi], stream=stream)
+        spec = g.make_spec(horizon=K, reach=goal, pessimistic=pess)
+        t_sub = time.perf_counter()
+        q.put((i, g.imdp_server_submit(server, dev_models[mi], spec), t_sub, models_h[mi].n_states))
+    q.put(None)
+    th.join()
+    clk = clocks.stop()
+    lat = np.array([(d[2] - (t0 + a)) * 1e3 for d, a in zip(done, arrivals)])
+    ok = all(d[0] == g.IMDP_OK and d[1] == r[1] for d, r in zip(done, reqs))
+    span = max(d[2] for d in done) - t0
+    units = float(sum(models_h[r[0]].nnz * r[1] for r in reqs))
+    server.close()
+    if rank != 0:
+        return
+    out = {
+        "metric": "served robust value iteration: transition-updates/s and arrival-to-result latency",
+        "value": units / span, "unit": UNIT, "n_gpus": world, "steps": n_req, "warmup": 1,
+        "ms_per_step": span * 1e3 / n_req, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic (seeded banded IMDPs, log-uniform shapes)",
+        "config": {"workload": f"served_poisson{int(args.rate)}", "requests": n_req, "rate_per_s": args.rate,
+                   "new_models": len(models_h), "shapes": "states log-U[50,4000], actions U{1..3}, "
+                   "window log-U[3,700], K U{100..500}", "server_budget_gb": args.server_budget_gb,
+                   "all_ok": bool(ok)},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                       "p99": float(np.percentile(lat, 99)), "mean": float(lat.mean()), "max": float(lat.max())},
+        "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,6 +536,9 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="storage of the transition bounds")
+    ap.add_argument("--requests", type=int, default=2000, help="served workload: number of requests")
+    ap.add_argument("--rate", type=float, default=2000.0, help="served workload: Poisson arrival rate per second")
+    ap.add_argument("--server-budget-gb", type=float, default=16.0, help="served workload: HBM budget of the server")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
@@ -380,7 +551,12 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload.startswith("uneven"):
+            run_uneven(args, rank, world, local_rank)
+        elif args.workload.startswith("served"):
+            run_served(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch

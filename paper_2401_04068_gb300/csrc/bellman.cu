@@ -232,10 +232,49 @@ struct Bounds {
   }
 };
 
+// One pass of the warm start over a column: acc = sum of V times (upper below
+// v_k, lower elsewhere), flt = gap sum of the entries below v_k, geq = gap sum of
+// the entries at v_k. The trip count is warp-uniform; padding entries read row 0
+// and contribute zero. With `carry` the per-lane gap sums count their wraps and
+// saturate; without it the column is narrow (all its gaps add up to < 2^64), so
+// no sum can wrap.
+template <bool carry, bool f32>
+__device__ __forceinline__ void warm_pass(const int32_t* rows, const Bounds<f32> lg, int32_t k,
+                                          const uint64_t* __restrict__ V, uint64_t vk, bool pess, int lane,
+                                          uint64_t& acc, uint64_t& flt, uint64_t& geq) {
+  uint32_t fc = 0, gc = 0;
+  const int nb = (k + 31) >> 5;
+#pragma unroll 2
+  for (int it = 0; it < nb; ++it) {
+    const int idx = it * 32 + lane;
+    const bool ok = idx < k;
+    const uint64_t v = __ldg(V + (ok ? rows[idx] : 0));
+    const ulonglong2 b = ok ? lg[idx] : make_ulonglong2(0, 0);
+    const bool below = pess ? (v < vk) : (v > vk);
+    acc += __umul64hi(v, b.x + (below ? b.y : 0ull));
+    const uint64_t gb = below ? b.y : 0ull, ge = v == vk ? b.y : 0ull;
+    flt += gb;
+    geq += ge;
+    if (carry) {
+      fc += flt < gb ? 1u : 0u;
+      gc += geq < ge ? 1u : 0u;
+    }
+  }
+  if (carry) {
+    flt = fc ? ~0ull : flt;
+    geq = gc ? ~0ull : geq;
+  }
+}
+
+// `rem_word` is rem = 1 - sum(lower) in Q1.63 (<= 2^63); when 0 < rem < 2^63 and
+// the column's gaps add up to < 2^64 ("narrow"), model creation sets bit 63 as a
+// flag on top of rem.
 template <bool f32>
-__device__ uint64_t column_q(const int32_t* rows, const Bounds<f32> lg, int32_t k, uint64_t rem,
+__device__ uint64_t column_q(const int32_t* rows, const Bounds<f32> lg, int32_t k, uint64_t rem_word,
                              const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane, int32_t hint,
                              int32_t* hint_out) {
+  const bool narrow = (rem_word >> 63) && (rem_word << 1);
+  const uint64_t rem = narrow ? (rem_word & (kOne - 1)) : rem_word;
   auto key_of = [&](int idx) -> uint64_t {
     const uint64_t v = __ldg(V + rows[idx]);
     return pess ? v : (kOne - v);
@@ -260,25 +299,12 @@ __device__ uint64_t column_q(const int32_t* rows, const Bounds<f32> lg, int32_t 
   if (hint >= 0 && hint < k) {
     const uint64_t vk = __ldg(V + rows[hint]);
     uint64_t acc = 0, flt = 0, geq = 0;
-    uint32_t fc = 0, gc = 0;
-    // warp-uniform trip count; padding entries read row 0 and contribute zero
-    const int nb = (k + 31) >> 5;
-#pragma unroll 4
-    for (int it = 0; it < nb; ++it) {
-      const int idx = it * 32 + lane;
-      const bool ok = idx < k;
-      const uint64_t v = __ldg(V + (ok ? rows[idx] : 0));
-      const ulonglong2 b = ok ? lg[idx] : make_ulonglong2(0, 0);
-      const bool below = pess ? (v < vk) : (v > vk);
-      acc += __umul64hi(v, b.x + (below ? b.y : 0ull));
-      const uint64_t gb = below ? b.y : 0ull, ge = v == vk ? b.y : 0ull;
-      flt += gb;
-      fc += flt < gb ? 1u : 0u;
-      geq += ge;
-      gc += geq < ge ? 1u : 0u;
-    }
-    flt = warp_sum_sat(fc ? ~0ull : flt);
-    geq = warp_sum_sat(gc ? ~0ull : geq);
+    if (narrow)
+      warm_pass<false>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
+    else
+      warm_pass<true>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
+    flt = warp_sum_sat(flt);
+    geq = warp_sum_sat(geq);
     if (flt < rem && rem - flt <= geq) {
       *hint_out = hint;
       return warp_sum_u64(acc) + __umul64hi(vk, rem - flt);

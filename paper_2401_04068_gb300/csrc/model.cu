@@ -18,6 +18,15 @@ namespace {
 constexpr double kFeasTol = 1e-12;
 enum : unsigned { kErrStruct = 1u, kErrInfeasible = 2u };
 
+// Per-column word of the Bellman kernel: rem = 1 - sum(lower) in Q1.63 (0 when
+// the lower bounds reach 1), with bit 63 set on top of it when 0 < rem < 2^63
+// and the column's gaps add up to less than 2^64 (saturated sum `gsum`): the
+// kernel then sums gaps without wrap checks.
+__device__ __forceinline__ unsigned long long rem_word(unsigned long long lsum, unsigned long long gsum) {
+  const unsigned long long r = lsum >= kOne ? 0ull : kOne - lsum;
+  return (r > 0 && r < kOne && gsum != ~0ull) ? (r | kOne) : r;
+}
+
 // One warp per column: range/order checks of the destinations, bound checks,
 // binary64 sums for the feasibility test, and the fixed-point conversion.
 __global__ void convert_columns_kernel(int32_t n_states, int32_t n_cols, const int32_t* __restrict__ colptr,
@@ -29,7 +38,7 @@ __global__ void convert_columns_kernel(int32_t n_states, int32_t n_cols, const i
   for (int32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n_cols; j += warps) {
     const int32_t a = colptr[j], b = colptr[j + 1];
     double slo = 0.0, sup = 0.0;
-    unsigned long long lsum = 0;
+    unsigned long long lsum = 0, gsum = 0;
     unsigned bad = 0;
     for (int32_t i = a + lane; i < b; i += 32) {
       const int32_t r = rowval[i];
@@ -46,6 +55,7 @@ __global__ void convert_columns_kernel(int32_t n_states, int32_t n_cols, const i
       const unsigned long long L = __double2ull_rn(lo * 9223372036854775808.0);
       const unsigned long long U = __double2ull_rn(up * 9223372036854775808.0);
       lg[i] = make_ulonglong2(L, U - L);
+      gsum = gsum + (U - L) < gsum ? ~0ull : gsum + (U - L);
       const unsigned long long t = lsum + L;
       if (t < lsum) bad |= kErrInfeasible;  // sum of lower bounds far above 1
       lsum = t;
@@ -57,11 +67,13 @@ __global__ void convert_columns_kernel(int32_t n_states, int32_t n_cols, const i
       const unsigned long long t = __shfl_xor_sync(0xffffffffu, lsum, o);
       if (lsum + t < lsum) bad |= kErrInfeasible;
       lsum += t;
+      const unsigned long long g = __shfl_xor_sync(0xffffffffu, gsum, o);
+      gsum = gsum + g < gsum ? ~0ull : gsum + g;
       bad |= __shfl_xor_sync(0xffffffffu, bad, o);
     }
     if (lane == 0) {
       if (slo > 1.0 + kFeasTol || sup < 1.0 - kFeasTol) bad |= kErrInfeasible;
-      rem[j] = lsum >= kOne ? 0ull : kOne - lsum;
+      rem[j] = rem_word(lsum, gsum);
       if (bad) atomicOr(err, bad);
     }
   }
@@ -96,7 +108,7 @@ __global__ void quantize_columns_kernel(int32_t n_cols, const int32_t* __restric
     sh = sh > 31 ? 31 : sh;
     const int down = 32 - sh;                                  // Q1.63 = m << down
     const unsigned long long half = 1ull << (down - 1);
-    unsigned long long lsum = 0;
+    unsigned long long lsum = 0, gsum = 0;
     double e = 0.0;
     for (int32_t i = a + lane; i < b; i += 32) {
       const unsigned long long L = lg[i].x, U = lg[i].x + lg[i].y;
@@ -107,16 +119,19 @@ __global__ void quantize_columns_kernel(int32_t n_cols, const int32_t* __restric
       lg32[i] = make_uint2((unsigned)mL, (unsigned)(mU - mL));
       const unsigned long long Lq = mL << down, Uq = mU << down;
       lsum += Lq;
+      gsum = gsum + (Uq - Lq) < gsum ? ~0ull : gsum + (Uq - Lq);
       e += (double)(Lq > L ? Lq - L : L - Lq) + (double)(Uq > U ? Uq - U : U - Uq);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+      const unsigned long long g = __shfl_xor_sync(0xffffffffu, gsum, o);
+      gsum = gsum + g < gsum ? ~0ull : gsum + g;
       e += __shfl_xor_sync(0xffffffffu, e, o);
     }
     if (lane == 0) {
       shift[j] = sh;
-      rem[j] = lsum >= kOne ? 0ull : kOne - lsum;
+      rem[j] = rem_word(lsum, gsum);
       err[j] = e / 9223372036854775808.0;
     }
   }
