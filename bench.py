@@ -523,6 +523,65 @@ def run_served(args, rank, world, local_rank):
     print(json.dumps(out), flush=True)
 
 
+def run_state_sharded(args, rank, world, local_rank):
+    """One model (default: the pimdp_2 shape) split by states over the ranks; every
+    rank iterates its slice and the ranks all-gather the iterates after each step
+    (strong scaling: the total work is fixed)."""
+    import torch
+    import paper_2401_04068_gb300 as g
+    from paper_2401_04068_gb300.sharded import SliceRunner, gather_slices
+    dev = _gpu_setup(rank, world, local_rank)
+    m = make_workload(args.workload, 0, args.models)  # the same model on every rank
+    dtype = g.IMDP_F32 if args.dtype == "f32" else g.IMDP_F64
+    bounds = g.imdp_partition_states(m.n_states, m.stateptr, m.colptr, world)
+    lengths = np.diff(bounds)
+    runner = SliceRunner(m, bounds, rank, dict(horizon=args.horizon, reach=m.goal), dtype)
+
+    def one_step():
+        runner.reset()
+        for _ in range(args.horizon):
+            own = runner.step()
+            if world > 1:
+                runner.put(gather_slices(own, lengths, rank))
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        one_step()
+    t1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    V = np.zeros(m.n_states)
+    k = [0]
+    runner.read(V, k)
+    assert k[0] == args.horizon
+    units = float(m.nnz) * args.horizon * args.steps  # the whole model, once
+    elapsed_ms, _, _ = reduce_across_ranks(elapsed_ms, 0.0, 0.0, world, dev)
+    if rank != 0:
+        return
+    cfg = workload_config(args.workload, m, args.horizon)
+    cfg.update(parallelism=f"state-sharded x{world}", partition=[int(x) for x in bounds])
+    out = {
+        "metric": METRIC, "value": units / (elapsed_ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded banded IMDP shaped like the paper's benchmark table)", "config": cfg,
+        "clocks": clk, "exchange_bytes_per_step": int(8 * m.n_states * args.horizon) if world > 1 else 0,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -539,6 +598,8 @@ def main():
     ap.add_argument("--requests", type=int, default=2000, help="served workload: number of requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="served workload: Poisson arrival rate per second")
     ap.add_argument("--server-budget-gb", type=float, default=16.0, help="served workload: HBM budget of the server")
+    ap.add_argument("--shard", default="problems", choices=["problems", "states"],
+                    help="multi-GPU split: independent problems per rank (default) or one model's states")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
@@ -555,6 +616,8 @@ def main():
             run_uneven(args, rank, world, local_rank)
         elif args.workload.startswith("served"):
             run_served(args, rank, world, local_rank)
+        elif args.shard == "states":
+            run_state_sharded(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

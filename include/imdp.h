@@ -233,6 +233,46 @@ IMDP_API int64_t imdp_session_launches(const imdp_session* s);
 IMDP_API void imdp_session_destroy(imdp_session* s);
 
 /*
+ * State-sharded value iteration (one model split over several GPUs).
+ * Sec. 4 notes that the per-state problems of Eq. 2 are independent within an
+ * iteration: a slice that owns states [s0, s1) computes V_k[s0, s1) exactly as
+ * the whole model does, given all of V_{k-1}. The caller runs one session per
+ * slice, steps every session one iteration at a time, and after each step
+ * copies every slice's owned values into all other slices (an all-gather),
+ * using imdp_session_values_get / _put on device buffers. Finite horizons only
+ * (each slice would test convergence on its own states).
+ */
+
+/* Contiguous state ranges of about equal work (20 B per transition, 12 B per
+ * column, 20 B per state and iteration): bounds int32[n_parts + 1], bounds[0] =
+ * 0, bounds[n_parts] = n_states, every range non-empty. stateptr (n_states + 1)
+ * and colptr are the whole model's CSC arrays (host). Host-only; needs no
+ * device. IMDP_EINVAL unless 1 <= n_parts <= n_states. */
+IMDP_API imdp_status imdp_partition_states(int32_t n_states, const int32_t* stateptr, const int32_t* colptr,
+                                           int32_t n_parts, int32_t* bounds);
+
+/* Slice of an n_states model that owns states [s0, s1): stateptr has s1 - s0 + 1
+ * entries (starting at 0, ending at n_cols) and colptr / rowval / lower / upper
+ * hold the columns of those states only, in the layout of imdp_create_csc;
+ * rowval indexes the whole state space [0, n_states). Only owned states are
+ * updated by a session on the slice; the others hold what imdp_session_values_put
+ * writes (initially V_0). Validation and errors as imdp_create_csc. */
+IMDP_API imdp_status imdp_create_csc_slice(int32_t n_states, int32_t s0, int32_t s1, int32_t n_cols, int64_t nnz,
+                                           const int32_t* stateptr, const int32_t* colptr, const int32_t* rowval,
+                                           const double* lower, const double* upper, imdp_dtype dtype, void* stream,
+                                           imdp_model** out);
+
+/* Copy V_k[s0, s1) of problem `index` (k = iterations completed; V_0 after a
+ * reset) as raw 64-bit words (Q1.63 fixed point, or the affine-mapped value of
+ * a reward problem) to / from device memory `dst` / `src` (s1 - s0 words),
+ * asynchronously on `stream`. The words move between sessions of identical
+ * specifications only. IMDP_EINVAL for a bad index or range or host memory. */
+IMDP_API imdp_status imdp_session_values_get(imdp_session* s, int32_t index, int32_t k, int32_t s0, int32_t s1,
+                                             uint64_t* dst, void* stream);
+IMDP_API imdp_status imdp_session_values_put(imdp_session* s, int32_t index, int32_t k, int32_t s0, int32_t s1,
+                                             const uint64_t* src, void* stream);
+
+/*
  * Continuous-batching server. Requests (a resident model plus a specification)
  * share the Bellman launches of one slotted batch run by a worker thread: a
  * request is admitted when a slot (up to 1024) and enough of the server's device

@@ -29,7 +29,8 @@ EXPORTED = [
     "imdp_session_create", "imdp_session_reset", "imdp_session_step", "imdp_session_run", "imdp_session_read",
     "imdp_session_launches", "imdp_session_destroy", "imdp_value_iteration_noalloc",
     "imdp_server_create", "imdp_server_submit", "imdp_server_poll", "imdp_server_wait", "imdp_server_destroy",
-    "imdp_model_error_bound",
+    "imdp_model_error_bound", "imdp_partition_states", "imdp_create_csc_slice", "imdp_session_values_get",
+    "imdp_session_values_put",
 ]
 
 
@@ -111,6 +112,14 @@ def load(path: Optional[str] = None):
     lib.imdp_model_error_bound.restype = C.c_int
     lib.imdp_server_destroy.argtypes = [vp]
     lib.imdp_server_destroy.restype = None
+    lib.imdp_partition_states.argtypes = [C.c_int32, vp, vp, C.c_int32, vp]
+    lib.imdp_partition_states.restype = C.c_int
+    lib.imdp_create_csc_slice.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64, vp, vp, vp, vp, vp,
+                                          C.c_int, vp, C.POINTER(vp)]
+    lib.imdp_create_csc_slice.restype = C.c_int
+    for f in ("imdp_session_values_get", "imdp_session_values_put"):
+        getattr(lib, f).argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, vp]
+        getattr(lib, f).restype = C.c_int
     for f in ("imdp_create_csc", "imdp_create_dense", "imdp_model_info", "imdp_value_iteration",
               "imdp_value_iteration_batch", "imdp_session_create", "imdp_session_reset", "imdp_session_step",
               "imdp_session_run", "imdp_session_read"):
@@ -425,3 +434,52 @@ def value_iteration(model: Model, n_states: int, policy: bool = False, stream=No
     k = [0]
     st = imdp_value_iteration(model, spec, V, k, res, pol, stream)
     return STATUS_NAMES[st], V, k[0], res, pol
+
+
+# ---------------------------------------------------------------- state sharding
+
+def imdp_partition_states(n_states: int, stateptr, colptr, n_parts: int) -> np.ndarray:
+    """Contiguous state ranges of about equal work: int32[n_parts + 1] bounds (host-only call)."""
+    sp = np.ascontiguousarray(stateptr, dtype=np.int32)
+    cp = np.ascontiguousarray(colptr, dtype=np.int32)
+    out = np.zeros(int(n_parts) + 1, np.int32)
+    _check(load().imdp_partition_states(int(n_states), _ptr(sp), _ptr(cp), int(n_parts), _ptr(out)),
+           "imdp_partition_states")
+    return out
+
+
+def imdp_create_csc_slice(n_states: int, s0: int, s1: int, n_cols: int, nnz: int, stateptr, colptr, rowval, lower,
+                          upper, dtype=IMDP_F64, stream=None) -> Model:
+    out = C.c_void_p()
+    st = load().imdp_create_csc_slice(int(n_states), int(s0), int(s1), int(n_cols), int(nnz), _ptr(stateptr),
+                                      _ptr(colptr), _ptr(rowval), _ptr(lower), _ptr(upper), int(dtype),
+                                      _stream(stream), C.byref(out))
+    _check(st, "imdp_create_csc_slice")
+    return Model(out.value)
+
+
+def imdp_session_values_get(s: Session, index: int, k: int, s0: int, s1: int, dst, stream=None):
+    _check(load().imdp_session_values_get(C.c_void_p(s.handle), int(index), int(k), int(s0), int(s1), _ptr(dst),
+                                          _stream(stream)), "imdp_session_values_get")
+
+
+def imdp_session_values_put(s: Session, index: int, k: int, s0: int, s1: int, src, stream=None):
+    _check(load().imdp_session_values_put(C.c_void_p(s.handle), int(index), int(k), int(s0), int(s1), _ptr(src),
+                                          _stream(stream)), "imdp_session_values_put")
+
+
+def slice_arrays(m, s0: int, s1: int):
+    """Host CSC arrays of the columns of states [s0, s1) of a model (rowval keeps
+    whole-model state indices): (stateptr, colptr, rowval, lower, upper)."""
+    c0, c1 = int(m.stateptr[s0]), int(m.stateptr[s1])
+    e0, e1 = int(m.colptr[c0]), int(m.colptr[c1])
+    return (np.ascontiguousarray(m.stateptr[s0:s1 + 1] - c0, dtype=np.int32),
+            np.ascontiguousarray(m.colptr[c0:c1 + 1] - e0, dtype=np.int32),
+            np.ascontiguousarray(m.rowval[e0:e1], dtype=np.int32),
+            np.ascontiguousarray(m.lower[e0:e1], dtype=np.float64),
+            np.ascontiguousarray(m.upper[e0:e1], dtype=np.float64))
+
+
+def create_model_slice(m, s0: int, s1: int, dtype=IMDP_F64, stream=None) -> Model:
+    sp, cp, rv, lo, up = slice_arrays(m, s0, s1)
+    return imdp_create_csc_slice(m.n_states, s0, s1, len(cp) - 1, len(rv), sp, cp, rv, lo, up, dtype, stream)

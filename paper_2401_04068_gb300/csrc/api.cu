@@ -26,6 +26,8 @@ struct DeviceGuard {
   }
 };
 
+}  // namespace
+
 bool have_device() {
   int n = 0;
   if (cudaGetDeviceCount(&n) != cudaSuccess) {
@@ -34,8 +36,6 @@ bool have_device() {
   }
   return n > 0;
 }
-
-}  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 

@@ -94,7 +94,7 @@ struct Stage {
   int32_t active;                        //                      the problem still runs
   int32_t k_iter;                        //                      iteration being computed
   int32_t fixed_off;                     //                      offset of state s0 in `fixed`
-  unsigned int done;                     // column slots of this tile finished so far
+  unsigned int done;                     // slots of this tile finished so far
 };
 
 struct Smem {
@@ -269,47 +269,56 @@ __device__ __forceinline__ void warm_pass(const int32_t* rows, const Bounds<f32>
 // `rem_word` is rem = 1 - sum(lower) in Q1.63 (<= 2^63); when 0 < rem < 2^63 and
 // the column's gaps add up to < 2^64 ("narrow"), model creation sets bit 63 as a
 // flag on top of rem.
+__device__ __forceinline__ uint64_t rem_of(uint64_t rem_word) {
+  return ((rem_word >> 63) && (rem_word << 1)) ? (rem_word & (kOne - 1)) : rem_word;
+}
+__device__ __forceinline__ bool narrow_of(uint64_t rem_word) { return (rem_word >> 63) && (rem_word << 1); }
+
+// Warm start. Decides the column without a search when rem = 0 (every entry keeps
+// its lower bound) or when last iteration's threshold entry `hint` still holds
+// the threshold: with kappa its key it does exactly when F(< kappa) < rem <=
+// F(<= kappa), F being the gap sum; then one pass gives q. Comparisons run on V
+// itself: key < kappa is V < V_kappa for a pessimistic adversary, V > V_kappa for
+// an optimistic one. Returns true with *q set (Q2.62) when decided.
 template <bool f32>
-__device__ uint64_t column_q(const int32_t* rows, const Bounds<f32> lg, int32_t k, uint64_t rem_word,
-                             const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane, int32_t hint,
-                             int32_t* hint_out) {
-  const bool narrow = (rem_word >> 63) && (rem_word << 1);
-  const uint64_t rem = narrow ? (rem_word & (kOne - 1)) : rem_word;
+__device__ __forceinline__ bool column_warm(const int32_t* rows, const Bounds<f32> lg, int32_t k, uint64_t rem_word,
+                                            const uint64_t* __restrict__ V, bool pess, int lane, int32_t hint,
+                                            uint64_t* q) {
+  const uint64_t rem = rem_of(rem_word);
+  if (rem == 0) {
+    uint64_t acc = 0;
+#pragma unroll 4
+    for (int idx = lane; idx < k; idx += 32) acc += __umul64hi(__ldg(V + rows[idx]), lg[idx].x);
+    *q = warp_sum_u64(acc);
+    return true;
+  }
+  if (hint < 0 || hint >= k) return false;
+  const uint64_t vk = __ldg(V + rows[hint]);
+  uint64_t acc = 0, flt = 0, geq = 0;
+  if (narrow_of(rem_word))
+    warm_pass<false>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
+  else
+    warm_pass<true>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
+  flt = warp_sum_sat(flt);
+  geq = warp_sum_sat(geq);
+  if (flt < rem && rem - flt <= geq) {
+    *q = warp_sum_u64(acc) + __umul64hi(vk, rem - flt);
+    return true;
+  }
+  return false;
+}
+
+// Threshold search over a column with rem > 0 (the warm start failed or had no
+// hint). Returns q in Q2.62 and the threshold entry in *hint_out.
+template <bool f32>
+__device__ uint64_t column_search(const int32_t* rows, const Bounds<f32> lg, int32_t k, uint64_t rem_word,
+                                  const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane,
+                                  int32_t* hint_out) {
+  const uint64_t rem = rem_of(rem_word);
   auto key_of = [&](int idx) -> uint64_t {
     const uint64_t v = __ldg(V + rows[idx]);
     return pess ? v : (kOne - v);
   };
-
-  if (rem == 0) {  // nothing to hand out: every entry keeps its lower bound
-    uint64_t acc = 0;
-#pragma unroll 4
-    for (int idx = lane; idx < k; idx += 32) {
-      const uint64_t key = key_of(idx);
-      acc += __umul64hi(pess ? key : (kOne - key), lg[idx].x);
-    }
-    *hint_out = hint;
-    return warp_sum_u64(acc);
-  }
-
-  // 1. warm start: does last iteration's threshold entry still hold it? With
-  // kappa its key, it does exactly when F(< kappa) < rem <= F(<= kappa), F being
-  // the gap sum; then this one pass gives q. Comparisons run on V itself:
-  // key < kappa is V < V_kappa for a pessimistic adversary, V > V_kappa for an
-  // optimistic one.
-  if (hint >= 0 && hint < k) {
-    const uint64_t vk = __ldg(V + rows[hint]);
-    uint64_t acc = 0, flt = 0, geq = 0;
-    if (narrow)
-      warm_pass<false>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
-    else
-      warm_pass<true>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
-    flt = warp_sum_sat(flt);
-    geq = warp_sum_sat(geq);
-    if (flt < rem && rem - flt <= geq) {
-      *hint_out = hint;
-      return warp_sum_u64(acc) + __umul64hi(vk, rem - flt);
-    }
-  }
 
   // 2. key range
   uint64_t lmin = ~0ull, lmax = 0;
@@ -470,6 +479,19 @@ __device__ uint64_t column_q(const int32_t* rows, const Bounds<f32> lg, int32_t 
   return acc + warp_sum_u64(extra);
 }
 
+// One column, warm start first: q in Q2.62, the threshold entry in *hint_out.
+template <bool f32>
+__device__ uint64_t column_q(const int32_t* rows, const Bounds<f32> lg, int32_t k, uint64_t rem_word,
+                             const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane, int32_t hint,
+                             int32_t* hint_out) {
+  uint64_t q;
+  if (column_warm<f32>(rows, lg, k, rem_word, V, pess, lane, hint, &q)) {
+    *hint_out = hint;
+    return q;
+  }
+  return column_search<f32>(rows, lg, k, rem_word, V, pess, ws, lane, hint_out);
+}
+
 // ---------------------------------------------------------------- the step kernel
 
 __device__ __forceinline__ bool problem_active(const StepLaunch& L, int p, int32_t* k_iter) {
@@ -492,6 +514,84 @@ __device__ __forceinline__ void finish_state(const Problem& P, int32_t s, int32_
     const uint64_t vold = Vin[s];
     const uint64_t d = vnew > vold ? vnew - vold : vold - vnew;
     dmax = d > dmax ? d : dmax;
+  }
+}
+
+// Best action of a state over columns [jb, je): first index attaining the optimum.
+template <class QAt>
+__device__ __forceinline__ void best_action(const Problem& P, int32_t jb, int32_t je, QAt q_at, uint64_t* bestq,
+                                            int32_t* best) {
+  uint64_t bq = 0;
+  int32_t bb = -1;
+  for (int32_t jj = jb; jj < je; ++jj) {
+    const uint64_t q = q_at(jj);
+    if (bb < 0 || (P.maximize ? q > bq : q < bq)) {
+      bq = q;
+      bb = jj - jb;
+    }
+  }
+  *bestq = bq;
+  *best = bb;
+}
+
+// State epilogue of a tile (one warp): opt over actions, reach/avoid mask,
+// reward update, V / policy / residual. `fixed_at(s)` gives the mask of state s,
+// `best_of(s, &q, &a)` the optimal action value and index.
+template <class FixedAt, class BestOf>
+__device__ void tile_epilogue(const StepLaunch& L, const Problem& P, const Tile& T, int32_t k_iter, int lane,
+                              FixedAt fixed_at, BestOf best_of) {
+  const uint64_t* __restrict__ Vin = P.V[(k_iter - 1) & 1];
+  uint64_t* __restrict__ Vout = P.V[k_iter & 1];
+  unsigned long long dmax = 0;
+  for (int32_t s = T.s0 + lane; s < T.s1; s += 32) {
+    const uint8_t fx = fixed_at(s);
+    uint64_t vnew;
+    int32_t best = -1;
+    if (fx == 1) {
+      vnew = kOne;
+    } else if (fx == 2) {
+      vnew = 0;
+    } else {
+      uint64_t bestq;
+      best_of(s, &bestq, &best);
+      if (P.property == kPropReward) {
+        // W_k = c_s + gamma * T(W_{k-1}) in signed Q2.62, clamped to [0, 1]
+        const int64_t tt = (int64_t)(__umul64hi(P.gamma_fix, bestq) << 1);
+        int64_t w = P.rbias[s] + tt;
+        w = w < 0 ? 0 : (w > (int64_t)(kOne >> 1) ? (int64_t)(kOne >> 1) : w);
+        vnew = (uint64_t)w << 1;
+      } else {
+        vnew = bestq >= (kOne >> 1) ? kOne : (bestq << 1);  // Q2.62 -> Q1.63, clamp at 1
+      }
+    }
+    finish_state(P, s, k_iter, vnew, best, Vin, Vout, dmax);
+  }
+  if (P.infinite) {
+    const uint64_t m = warp_max_u64(dmax);
+    if (lane == 0 && m) atomicMax(&L.its[T.p].resmax, (unsigned long long)m);
+  }
+}
+
+// One column of a staged tile: leaves q in st.q[li] and updates the hint.
+template <bool f32>
+__device__ __forceinline__ void stage_column(Stage& st, const Tile& T, int32_t li, int32_t k_iter, WarpScratch* ws,
+                                             int lane) {
+  const Problem& P = st.prob;
+  const int32_t c = T.c0 + li;
+  const int32_t eb = T.e0 & ~3, cb = T.c0 & ~3, mb = T.c0 & ~1;
+  const int32_t ca = st.cptr[c - cb], ce = st.cptr[c + 1 - cb];
+  const int32_t h = P.hint ? st.hint[c - cb] : -1;
+  Bounds<f32> bd;
+  if (f32)
+    bd = Bounds<f32>{reinterpret_cast<const uint2*>(st.lg) + (ca - (T.e0 & ~1)), 32 - st.shift[c - cb]};
+  else
+    bd = Bounds<f32>{st.lg + (ca - T.e0), 0};
+  int32_t hout;
+  const uint64_t q = column_q<f32>(st.rows + (ca - eb), bd, ce - ca, st.rem[c - mb], P.V[(k_iter - 1) & 1],
+                                   P.pessimistic != 0, ws, lane, h, &hout);
+  if (lane == 0) {
+    st.q[li] = q;
+    if (P.hint && hout != h) P.hint[c] = hout;
   }
 }
 
@@ -583,13 +683,14 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
     // ------------------------------------------------------------ consumers
     // The CTA's tiles t_j = blockIdx.x + j*gridDim.x are visited in order by
     // every consumer warp: wait until tile j has landed, work on its own slots,
-    // arrive on the stage's "empty" barrier. Slots (one per column; one for a
-    // tile read from global memory) are dealt round-robin across tiles, so a
-    // warp that has no column left in tile j moves on to tile j+1 while the
-    // others finish. Because every warp visits every tile, no warp can fall two
-    // rounds behind a stage, which keeps the parity waits unambiguous. The warp
-    // that completes a tile's last slot runs the tile's state epilogue before it
-    // arrives, so the producer refills a stage only after the epilogue.
+    // arrive on the stage's "empty" barrier. A slot is a column, or a whole
+    // tile read from global memory. Slots are dealt
+    // round-robin across tiles, so a warp that has nothing left in tile j moves
+    // on to tile j+1 while the others finish. Because every warp visits every
+    // tile, no warp can fall two rounds behind a stage, which keeps the parity
+    // waits unambiguous. The warp that completes a tile's last slot runs the
+    // tile's state epilogue before it arrives, so the producer refills a stage
+    // only after the epilogue.
     WarpScratch* ws = &S.ws[warp];
     int32_t slot_base = 0;  // global slot index of tile j's first slot
     int j = 0;
@@ -611,26 +712,10 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
       for (int32_t ls = first; ls < nslots; ls += kConsumerWarps) {
         if (active) {
           if (!T.big) {
-            const Problem& P = st.prob;
-            const int32_t c = T.c0 + ls;
-            const int32_t eb = T.e0 & ~3, cb = T.c0 & ~3, mb = T.c0 & ~1;
-            const int32_t ca = st.cptr[c - cb], ce = st.cptr[c + 1 - cb];
-            const int32_t h = P.hint ? st.hint[c - cb] : -1;
-            int32_t hout;
-            uint64_t q;
-            if (P.lg32) {
-              const Bounds<true> bd{reinterpret_cast<const uint2*>(st.lg) + (ca - (T.e0 & ~1)), 32 - st.shift[c - cb]};
-              q = column_q<true>(st.rows + (ca - eb), bd, ce - ca, st.rem[c - mb], P.V[(k_iter - 1) & 1],
-                                 P.pessimistic != 0, ws, lane, h, &hout);
-            } else {
-              const Bounds<false> bd{st.lg + (ca - T.e0), 0};
-              q = column_q<false>(st.rows + (ca - eb), bd, ce - ca, st.rem[c - mb], P.V[(k_iter - 1) & 1],
-                                  P.pessimistic != 0, ws, lane, h, &hout);
-            }
-            if (lane == 0) {
-              st.q[ls] = q;
-              if (P.hint && hout != h) P.hint[c] = hout;
-            }
+            if (st.prob.lg32)
+              stage_column<true>(st, T, ls, k_iter, ws, lane);
+            else
+              stage_column<false>(st, T, ls, k_iter, ws, lane);
           } else {
             // one state too large for a stage: this warp reads its columns from global memory
             const Problem& P = L.probs[T.p];
@@ -673,49 +758,21 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
         if (prev + 1 == (unsigned)nslots) {
           __threadfence_block();
           if (active) {
-            const Problem& P = T.big ? L.probs[T.p] : st.prob;
-            const uint64_t* __restrict__ Vin = P.V[(k_iter - 1) & 1];
-            uint64_t* __restrict__ Vout = P.V[k_iter & 1];
-            unsigned long long dmax = 0;
-            const int32_t sb = T.s0 & ~3;
-            for (int32_t s = T.s0 + lane; s < T.s1; s += 32) {
-              const uint8_t fx = T.big ? P.fixed[s] : st.fixed[st.fixed_off + (s - T.s0)];
-              uint64_t vnew;
-              int32_t best = -1;
-              if (fx == 1) {
-                vnew = kOne;
-              } else if (fx == 2) {
-                vnew = 0;
-              } else {
-                uint64_t bestq = 0;
-                if (T.big) {
-                  bestq = st.q[0];
-                  best = (int32_t)(long long)st.q[1];
-                } else {
-                  const int32_t jb = st.sptr[s - sb], je = st.sptr[s + 1 - sb];
-                  for (int32_t jj = jb; jj < je; ++jj) {
-                    const uint64_t q = st.q[jj - T.c0];
-                    if (best < 0 || (P.maximize ? q > bestq : q < bestq)) {
-                      bestq = q;
-                      best = jj - jb;
-                    }
-                  }
-                }
-                if (P.property == kPropReward) {
-                  // W_k = c_s + gamma * T(W_{k-1}) in signed Q2.62, clamped to [0, 1]
-                  const int64_t t = (int64_t)(__umul64hi(P.gamma_fix, bestq) << 1);
-                  int64_t w = P.rbias[s] + t;
-                  w = w < 0 ? 0 : (w > (int64_t)(kOne >> 1) ? (int64_t)(kOne >> 1) : w);
-                  vnew = (uint64_t)w << 1;
-                } else {
-                  vnew = bestq >= (kOne >> 1) ? kOne : (bestq << 1);  // Q2.62 -> Q1.63, clamp at 1
-                }
-              }
-              finish_state(P, s, k_iter, vnew, best, Vin, Vout, dmax);
-            }
-            if (P.infinite) {
-              const uint64_t m = warp_max_u64(dmax);
-              if (lane == 0 && m) atomicMax(&L.its[T.p].resmax, (unsigned long long)m);
+            if (T.big) {
+              const Problem& P = L.probs[T.p];
+              const uint64_t bq = st.q[0];
+              const int32_t bb = (int32_t)(long long)st.q[1];
+              tile_epilogue(L, P, T, k_iter, lane, [&](int32_t s) { return P.fixed[s]; },
+                            [&](int32_t, uint64_t* q, int32_t* b) { *q = bq; *b = bb; });
+            } else {
+              const Problem& P = st.prob;
+              const int32_t sb = T.s0 & ~3;
+              tile_epilogue(L, P, T, k_iter, lane,
+                            [&](int32_t s) { return st.fixed[st.fixed_off + (s - T.s0)]; },
+                            [&](int32_t s, uint64_t* bq, int32_t* bb) {
+                              const int32_t jb = st.sptr[s - sb], je = st.sptr[s + 1 - sb];
+                              best_action(P, jb, je, [&](int32_t jj) { return st.q[jj - T.c0]; }, bq, bb);
+                            });
             }
           }
           __syncwarp();
@@ -726,6 +783,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.empty[stage]);  // this warp is done with tile j
     }
+
   }
 
   // The last CTA to finish advances every running problem's iteration state.
@@ -773,8 +831,8 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
 void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out) {
   const std::vector<int32_t>& sp = m->h_stateptr;
   const std::vector<int32_t>& cp = m->h_colptr;
-  const int32_t n = m->n_states;
-  int32_t s = 0;
+  const int32_t n = m->own1;  // tiles cover the owned states only
+  int32_t s = m->own0;
   while (s < n) {
     Tile T;
     T.p = problem;

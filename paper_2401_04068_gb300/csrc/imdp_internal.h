@@ -53,6 +53,8 @@ struct DevModel {
   int32_t n_cols = 0;
   int64_t nnz = 0;
   int32_t max_col = 0;     // largest column (entries)
+  int32_t own0 = 0;        // states [own0, own1) have columns and are updated; the rest
+  int32_t own1 = 0;        // (a slice of a state-sharded model) only hold exchanged values
   int32_t dtype = IMDP_F64;
   int32_t* stateptr = nullptr;  // n_states + 1
   int32_t* colptr = nullptr;    // n_cols + 1
@@ -136,8 +138,10 @@ void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out);
 // model.cu
 imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, const int32_t* stateptr,
                              const int32_t* colptr, const int32_t* rowval, const double* lower,
-                             const double* upper, imdp_dtype dtype, cudaStream_t st, DevModel** out);
+                             const double* upper, imdp_dtype dtype, cudaStream_t st, DevModel** out,
+                             int32_t own0 = 0, int32_t own1 = -1);
 void model_destroy(DevModel* m);
+inline bool is_slice(const DevModel* m) { return m->own0 != 0 || m->own1 != m->n_states; }
 
 // session.cu: resident device state of value iteration for a batch of problems.
 // Padding of the per-state / per-column arrays so that 16-byte-aligned bulk-copy
@@ -191,6 +195,7 @@ void reward_map(const double* r, int32_t n, double g, int32_t K, bool infinite, 
 
 // api.cu
 void set_error(const std::string& msg);
+bool have_device();
 bool is_device_pointer(const void* p);
 imdp_status cuda_status(cudaError_t e, const char* where);
 

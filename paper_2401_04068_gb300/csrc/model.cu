@@ -161,11 +161,14 @@ void model_destroy(DevModel* m) {
 
 imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, const int32_t* stateptr,
                              const int32_t* colptr, const int32_t* rowval, const double* lower,
-                             const double* upper, imdp_dtype dtype, cudaStream_t st, DevModel** out) {
+                             const double* upper, imdp_dtype dtype, cudaStream_t st, DevModel** out,
+                             int32_t own0, int32_t own1) {
   if (!out) { set_error("out is NULL"); return IMDP_EINVAL; }
   *out = nullptr;
-  if (n_states < 1 || n_cols < n_states || nnz < 0 || nnz >= (int64_t(1) << 31)) {
-    set_error("dimensions out of range (need n_states >= 1, n_cols >= n_states, 0 <= nnz < 2^31)");
+  if (own1 < 0) own1 = n_states;
+  if (n_states < 1 || own0 < 0 || own1 > n_states || own0 >= own1 || n_cols < own1 - own0 || nnz < 0 ||
+      nnz >= (int64_t(1) << 31)) {
+    set_error("dimensions out of range (need n_states >= 1, n_cols >= owned states, 0 <= nnz < 2^31)");
     return IMDP_EINVAL;
   }
   if (!stateptr || !colptr || (nnz > 0 && (!rowval || !lower || !upper))) {
@@ -186,8 +189,11 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e, "sync");
   if (hs[0] != 0 || hs[n_states] != n_cols) { set_error("stateptr must start at 0 and end at n_cols"); return IMDP_EINVAL; }
-  for (int32_t s = 0; s < n_states; ++s)
-    if (hs[s + 1] <= hs[s]) { set_error("every state needs at least one action (stateptr strictly increasing)"); return IMDP_EINVAL; }
+  for (int32_t s = 0; s < n_states; ++s) {
+    const bool own = s >= own0 && s < own1;
+    if (own && hs[s + 1] <= hs[s]) { set_error("every state needs at least one action (stateptr strictly increasing)"); return IMDP_EINVAL; }
+    if (!own && hs[s + 1] != hs[s]) { set_error("states outside the slice carry no columns"); return IMDP_EINVAL; }
+  }
   if (hc[0] != 0 || hc[n_cols] != nnz) { set_error("colptr must start at 0 and end at nnz"); return IMDP_EINVAL; }
   int32_t max_col = 0;
   for (int32_t j = 0; j < n_cols; ++j) {
@@ -198,6 +204,8 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
 
   DevModel* m = new DevModel();
   m->n_states = n_states;
+  m->own0 = own0;
+  m->own1 = own1;
   m->n_cols = n_cols;
   m->nnz = nnz;
   m->max_col = max_col;

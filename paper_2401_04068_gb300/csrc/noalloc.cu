@@ -106,6 +106,7 @@ extern "C" IMDP_API imdp_status imdp_value_iteration_noalloc(imdp_model* m, cons
     set_error("imdp_value_iteration_noalloc: model has more than 131072 states (the fixed scratch limit)");
     return IMDP_EINVAL;
   }
+  if (is_slice(dm)) { set_error("slices of a state-sharded model run in sessions only"); return IMDP_EINVAL; }
   imdp_status s = check_spec(dm, spec);
   if (s != IMDP_OK) return s;
   if (spec->property == IMDP_REWARD) {

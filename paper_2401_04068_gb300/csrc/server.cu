@@ -463,6 +463,7 @@ imdp_status imdp_server_submit(imdp_server* srv, imdp_model* m, const imdp_spec*
   if (!srv || !m || !spec || !ticket) { set_error("NULL argument"); return IMDP_EINVAL; }
   Server* S = srv->s;
   if (m->device != S->device) { set_error("model and server must be on one device"); return IMDP_EINVAL; }
+  if (is_slice(m->dev)) { set_error("slices of a state-sharded model run in sessions only"); return IMDP_EINVAL; }
   imdp_status st = check_spec(m->dev, spec);
   if (st != IMDP_OK) return st;
   Request* r = new Request();

@@ -93,6 +93,10 @@ imdp_status check_spec(const DevModel* m, const imdp_spec* sp) {
       }
   }
   if (sp->horizon < 0) { set_error("horizon must be >= 0"); return IMDP_EINVAL; }
+  if (sp->infinite_time && is_slice(m)) {
+    // each slice would test convergence on its own states only
+    set_error("a state-sharded slice runs finite horizons only"); return IMDP_EINVAL;
+  }
   if (sp->infinite_time && !(sp->eps > 0.0)) { set_error("eps must be > 0 for an infinite horizon"); return IMDP_EINVAL; }
   if (sp->n_reach < 0 || (sp->n_reach > 0 && !sp->reach)) { set_error("bad reach set"); return IMDP_EINVAL; }
   if (sp->property == IMDP_REACH_AVOID && (sp->n_avoid < 0 || (sp->n_avoid > 0 && !sp->avoid))) {
