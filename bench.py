@@ -451,8 +451,11 @@ def run_uneven(args, rank, world, local_rank):
 def run_served(args, rank, world, local_rank):
     """Continuous-batching server under a Poisson request stream: requests arrive at
     `--rate` per second; 70 % bring a new model (created on arrival, inside the
-    measured latency), 30 % re-query a resident one. Latency = arrival to result."""
+    measured latency), 30 % re-query a resident one. Arrivals are handled by a
+    pool of `--client-threads` frontend threads (model creation + submit), each
+    on its own stream. Latency = arrival to result."""
     import queue as _queue
+    from concurrent.futures import Future, ThreadPoolExecutor
     import torch
     import paper_2401_04068_gb300 as g
     from workloads.imdp_synth import served_stream
@@ -485,18 +488,53 @@ def run_served(args, rank, world, local_rank):
 
     th = threading.Thread(target=waiter, daemon=True)
     th.start()
+    create_s = []
+    lag_s = []
+    lock = threading.Lock()
+    local = threading.local()
+    streams = [torch.cuda.Stream(device=dev) for _ in range(args.client_threads)]
+    next_stream = [0]
+
+    def model_for(mi):
+        # the first request of a model creates it; later ones wait for that
+        with lock:
+            f = dev_models[mi]
+            mine = f is None
+            if mine:
+                f = dev_models[mi] = Future()
+        if mine:
+            tc = time.perf_counter()
+            f.set_result(g.create_model(models_h[mi], stream=local.stream))
+            create_s.append(time.perf_counter() - tc)
+        return f.result()
+
+    def handle(i):
+        if not hasattr(local, "stream"):
+            torch.cuda.set_device(dev)
+            with lock:
+                local.stream = streams[next_stream[0] % len(streams)]
+                next_stream[0] += 1
+        mi, K, pess, goal = reqs[i]
+        model = model_for(mi)
+        spec = g.make_spec(horizon=K, reach=goal, pessimistic=pess)
+        t_sub = time.perf_counter()
+        q.put((i, g.imdp_server_submit(server, model, spec), t_sub, models_h[mi].n_states))
+
+    pool = ThreadPoolExecutor(max_workers=args.client_threads)
     clocks = ClockSampler(local_rank)
     clocks.start()
     t0 = time.perf_counter()
-    for i, (mi, K, pess, goal) in enumerate(reqs):
+    futs = []
+    for i in range(n_req):
         delay = t0 + arrivals[i] - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        if dev_models[mi] is None:
-            dev_models[mi] = g.create_model(models_h[mi], stream=stream)
-        spec = g.make_spec(horizon=K, reach=goal, pessimistic=pess)
-        t_sub = time.perf_counter()
-        q.put((i, g.imdp_server_submit(server, dev_models[mi], spec), t_sub, models_h[mi].n_states))
+        else:
+            lag_s.append(-delay)
+        futs.append(pool.submit(handle, i))
+    for f in futs:
+        f.result()
+    pool.shutdown()
     q.put(None)
     th.join()
     clk = clocks.stop()
@@ -513,11 +551,16 @@ def run_served(args, rank, world, local_rank):
         "ms_per_step": span * 1e3 / n_req, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic (seeded banded IMDPs, log-uniform shapes)",
         "config": {"workload": f"served_poisson{int(args.rate)}", "requests": n_req, "rate_per_s": args.rate,
-                   "new_models": len(models_h), "shapes": "states log-U[50,4000], actions U{1..3}, "
+                   "new_models": len(models_h), "client_threads": args.client_threads,
+                   "shapes": "states log-U[50,4000], actions U{1..3}, "
                    "window log-U[3,700], K U{100..500}", "server_budget_gb": args.server_budget_gb,
                    "all_ok": bool(ok)},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
                        "p99": float(np.percentile(lat, 99)), "mean": float(lat.mean()), "max": float(lat.max())},
+        "client": {"model_create_ms_mean": 1e3 * float(np.mean(create_s)) if create_s else 0.0,
+                   "model_create_s_total": float(np.sum(create_s)),
+                   "submits_behind_schedule": len(lag_s),
+                   "max_lag_ms": 1e3 * float(max(lag_s)) if lag_s else 0.0},
         "clocks": clk,
     }
     print(json.dumps(out), flush=True)
@@ -598,6 +641,7 @@ def main():
     ap.add_argument("--requests", type=int, default=2000, help="served workload: number of requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="served workload: Poisson arrival rate per second")
     ap.add_argument("--server-budget-gb", type=float, default=16.0, help="served workload: HBM budget of the server")
+    ap.add_argument("--client-threads", type=int, default=4, help="served workload: frontend threads")
     ap.add_argument("--shard", default="problems", choices=["problems", "states"],
                     help="multi-GPU split: independent problems per rank (default) or one model's states")
     args = ap.parse_args()

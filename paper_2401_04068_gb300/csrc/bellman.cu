@@ -27,6 +27,8 @@
 //   0. warm start: the entry that held the threshold in the previous iteration is
 //      tried first; one pass over the column checks F(<v) < rem <= F(<=v) exactly
 //      and, when it holds (the usual case once V settles), yields q directly;
+//      when it fails, one more pass tries the adjacent distinct key in the
+//      direction the sums point to (where most thresholds move);
 //   1. otherwise it gathers the keys and takes their min/max (redux.sync on
 //      32-bit halves);
 //   2. histograms the gaps (and counts) into 64 bins of [min, max] and scans the
@@ -280,10 +282,18 @@ __device__ __forceinline__ bool narrow_of(uint64_t rem_word) { return (rem_word 
 // F(<= kappa), F being the gap sum; then one pass gives q. Comparisons run on V
 // itself: key < kappa is V < V_kappa for a pessimistic adversary, V > V_kappa for
 // an optimistic one. Returns true with *q set (Q2.62) when decided.
+// What a failed warm start leaves for the neighbour check: the tried key's V,
+// the pass's dot product and its gap sums below and at that key.
+struct WarmMiss {
+  uint64_t vk, acc, flt, geq;
+  bool valid;
+};
+
 template <bool f32>
 __device__ __forceinline__ bool column_warm(const int32_t* rows, const Bounds<f32> lg, int32_t k, uint64_t rem_word,
                                             const uint64_t* __restrict__ V, bool pess, int lane, int32_t hint,
-                                            uint64_t* q) {
+                                            uint64_t* q, WarmMiss* miss) {
+  miss->valid = false;
   const uint64_t rem = rem_of(rem_word);
   if (rem == 0) {
     uint64_t acc = 0;
@@ -301,11 +311,80 @@ __device__ __forceinline__ bool column_warm(const int32_t* rows, const Bounds<f3
     warm_pass<true>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
   flt = warp_sum_sat(flt);
   geq = warp_sum_sat(geq);
+  acc = warp_sum_u64(acc);
   if (flt < rem && rem - flt <= geq) {
-    *q = warp_sum_u64(acc) + __umul64hi(vk, rem - flt);
+    *q = acc + __umul64hi(vk, rem - flt);
     return true;
   }
+  *miss = WarmMiss{vk, acc, flt, geq, true};
   return false;
+}
+
+// Neighbour check after a failed warm start at key kappa. If F(< kappa) >= rem the
+// threshold lies below kappa, else above it; in most misses it is the adjacent
+// distinct key. One pass finds that key (kappa- = the largest key below kappa, or
+// kappa+ = the smallest above), the gap sum G of its entries, and the change of
+// the warm pass's dot product when the entries between the two keys switch from
+// upper to lower bound (or back): D = sum (hi(V (L + G)) - hi(V L)). Then
+//   below: F(< kappa-) = F(< kappa) - G, holds when < rem;
+//   above: F(< kappa+) = F(<= kappa), holds when F(<= kappa) + G >= rem;
+// and q is the warm formula at the new key, to the bit. Returns false when the
+// threshold moved further (or a sum is not exact), leaving the full search.
+template <bool f32>
+__device__ __forceinline__ bool column_neighbor(const int32_t* rows, const Bounds<f32> lg, int32_t k, uint64_t rem,
+                                                const uint64_t* __restrict__ V, bool pess, int lane,
+                                                const WarmMiss& w, uint64_t* q, int32_t* hint_out) {
+  const bool down = w.flt >= rem;
+  if (down && w.flt >= kOne) return false;  // F(< kappa) clipped: not exact
+  const uint64_t kap = pess ? w.vk : kOne - w.vk;
+  uint64_t best = 0, gs = 0, ds = 0, dk = 0;
+  bool have = false;
+  int32_t bi = -1;
+  const int nb = (k + 31) >> 5;
+  for (int it = 0; it < nb; ++it) {
+    const int idx = it * 32 + lane;
+    if (idx >= k) break;
+    const uint64_t v = __ldg(V + rows[idx]);
+    const uint64_t key = pess ? v : kOne - v;
+    const ulonglong2 b = lg[idx];
+    const uint64_t d = __umul64hi(v, b.x + b.y) - __umul64hi(v, b.x);
+    const bool side = down ? key < kap : key > kap;
+    if (side) {
+      const bool better = !have || (down ? key > best : key < best);
+      if (better) {
+        best = key;
+        gs = b.y;
+        ds = d;
+        bi = idx;
+        have = true;
+      } else if (key == best) {
+        gs = sat_add(gs, b.y);
+        ds += d;
+      }
+    } else if (!down && key == kap) {
+      dk += d;
+    }
+  }
+  if (!__any_sync(kFull, have)) return false;
+  const uint64_t tgt = down ? warp_max_u64(have ? best : 0ull) : warp_min_u64(have ? best : ~0ull);
+  const bool mine = have && best == tgt;
+  const uint64_t G = warp_sum_sat(mine ? gs : 0ull);
+  const uint64_t D = warp_sum_u64(mine ? ds : 0ull);
+  const unsigned mm = __ballot_sync(kFull, mine);
+  const int32_t h = __shfl_sync(kFull, bi, __ffs(mm) - 1);
+  const uint64_t vt = pess ? tgt : kOne - tgt;
+  if (down) {
+    const uint64_t fl = w.flt - G;  // G <= F(< kappa) < 2^63
+    if (fl >= rem) return false;
+    *q = w.acc - D + __umul64hi(vt, rem - fl);
+  } else {
+    const uint64_t DK = warp_sum_u64(dk);
+    const uint64_t fl = w.flt + w.geq;  // < rem, exact
+    if (sat_add(fl, G) < rem) return false;
+    *q = w.acc + DK + __umul64hi(vt, rem - fl);
+  }
+  *hint_out = h;
+  return true;
 }
 
 // Threshold search over a column with rem > 0 (the warm start failed or had no
@@ -434,7 +513,8 @@ __device__ uint64_t column_search(const int32_t* rows, const Bounds<f32> lg, int
     if (m && first_cand < 0) first_cand = base + __ffs(m) - 1;
     if (!uniform) {
       if (cand) {
-        const unsigned at = pos + __popc(m & lt);
+        // < 32: a crossing bin of more than 32 entries was narrowed above
+        const unsigned at = min(pos + __popc(m & lt), 31u);
         ws->ck[at] = key;
         ws->cg[at] = b.y < rem ? b.y : rem;
         ws->ci[at] = idx;
@@ -449,6 +529,7 @@ __device__ uint64_t column_search(const int32_t* rows, const Bounds<f32> lg, int
     *hint_out = -1;
     return acc;
   }
+  pos = min(pos, 32u);
   const uint64_t r2 = rem - fb;  // > 0 by construction of the crossing bin
   if (uniform) {
     // one key for all candidates: they take min(r2, their total gap) together
@@ -484,12 +565,24 @@ template <bool f32>
 __device__ uint64_t column_q(const int32_t* rows, const Bounds<f32> lg, int32_t k, uint64_t rem_word,
                              const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane, int32_t hint,
                              int32_t* hint_out) {
+  // A hint of -2 - i names entry i as well and records that the column's last
+  // value came from the full search: its threshold is moving fast, so a miss
+  // goes to the search without trying the neighbour.
+  const bool moving = hint <= -2;
+  const int32_t entry = moving ? -2 - hint : hint;
   uint64_t q;
-  if (column_warm<f32>(rows, lg, k, rem_word, V, pess, lane, hint, &q)) {
-    *hint_out = hint;
+  WarmMiss miss;
+  if (column_warm<f32>(rows, lg, k, rem_word, V, pess, lane, entry, &q, &miss)) {
+    *hint_out = entry;
     return q;
   }
-  return column_search<f32>(rows, lg, k, rem_word, V, pess, ws, lane, hint_out);
+  if (miss.valid && !moving &&
+      column_neighbor<f32>(rows, lg, k, rem_of(rem_word), V, pess, lane, miss, &q, hint_out))
+    return q;
+  int32_t found;
+  q = column_search<f32>(rows, lg, k, rem_word, V, pess, ws, lane, &found);
+  *hint_out = found >= 0 ? -2 - found : -1;
+  return q;
 }
 
 // ---------------------------------------------------------------- the step kernel

@@ -137,10 +137,23 @@ __global__ void quantize_columns_kernel(int32_t n_cols, const int32_t* __restric
   }
 }
 
+// Staging buffer in stream order (cudaMallocAsync / cudaFreeAsync): creating a
+// model never waits for work that other streams have in flight (a plain
+// cudaFree would synchronize the whole device).
 struct DevBuf {
   void* p = nullptr;
+  cudaStream_t s = nullptr;
+  bool alloc(size_t bytes, cudaStream_t st) {
+    s = st;
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return false;
+    }
+    return true;
+  }
   ~DevBuf() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
   }
 };
 
@@ -233,14 +246,14 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
   const double* lo_d = lower;
   const double* up_d = upper;
   if (nnz > 0 && !is_device_pointer(lower)) {
-    if (cudaMalloc(&dlo.p, sizeof(double) * nz) != cudaSuccess) { cudaGetLastError(); model_destroy(m); set_error("staging allocation failed"); return IMDP_ENOMEM; }
+    if (!dlo.alloc(sizeof(double) * nz, st)) { model_destroy(m); set_error("staging allocation failed"); return IMDP_ENOMEM; }
     lo_d = (const double*)dlo.p;
   }
   if (nnz > 0 && !is_device_pointer(upper)) {
-    if (cudaMalloc(&dup.p, sizeof(double) * nz) != cudaSuccess) { cudaGetLastError(); model_destroy(m); set_error("staging allocation failed"); return IMDP_ENOMEM; }
+    if (!dup.alloc(sizeof(double) * nz, st)) { model_destroy(m); set_error("staging allocation failed"); return IMDP_ENOMEM; }
     up_d = (const double*)dup.p;
   }
-  if (cudaMalloc(&derr.p, sizeof(unsigned)) != cudaSuccess) { cudaGetLastError(); model_destroy(m); set_error("allocation failed"); return IMDP_ENOMEM; }
+  if (!derr.alloc(sizeof(unsigned), st)) { model_destroy(m); set_error("allocation failed"); return IMDP_ENOMEM; }
 
   e = cudaMemsetAsync(m->stateptr, 0, sizeof(int32_t) * ns_pad, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->colptr, 0, sizeof(int32_t) * nc_pad, st);
@@ -283,7 +296,7 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
     DevBuf derr2;
     if (cudaMalloc(&m->lg32, sizeof(uint2) * nz32) != cudaSuccess ||
         cudaMalloc(&m->shift, sizeof(int32_t) * nc_pad) != cudaSuccess ||
-        cudaMalloc(&derr2.p, sizeof(double) * n_cols) != cudaSuccess) {
+        !derr2.alloc(sizeof(double) * n_cols, st)) {
       cudaGetLastError();
       model_destroy(m);
       set_error("device allocation failed for 32-bit storage");
