@@ -492,7 +492,8 @@ def run_served(args, rank, world, local_rank):
     lag_s = []
     lock = threading.Lock()
     local = threading.local()
-    streams = [torch.cuda.Stream(device=dev) for _ in range(args.client_threads)]
+    # high priority: a new model's conversion kernel runs before the server's queued launches
+    streams = [torch.cuda.Stream(device=dev, priority=-1) for _ in range(args.client_threads)]
     next_stream = [0]
 
     def model_for(mi):

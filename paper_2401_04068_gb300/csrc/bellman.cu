@@ -5,7 +5,9 @@
 //
 // Data movement. The launch is persistent (one CTA per SM). The model is cut into
 // state-aligned tiles (consecutive states of one problem, <= kTileEntries
-// entries). A producer warp streams each tile's destination indices and bound
+// entries); states that do not fit a stage or that have columns of kWideCol
+// entries or more are "wide" and run in bellman_wide_kernel (a whole CTA per
+// state, launched just before). A producer warp streams each tile's destination indices and bound
 // pairs into a three-stage shared-memory ring with bulk asynchronous copies
 // (cp.async.bulk, completion counted on an mbarrier), while fifteen consumer
 // warps work on the tiles already landed (16 warps: four per SM sub-partition,
@@ -688,6 +690,8 @@ __device__ __forceinline__ void stage_column(Stage& st, const Tile& T, int32_t l
   }
 }
 
+__device__ void end_of_launch(const StepLaunch& L, int* is_last);
+
 __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaunch L) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem& S = *reinterpret_cast<Smem*>(smem_raw);
@@ -726,7 +730,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
         st.tile = T;
         st.active = act ? 1 : 0;
         st.k_iter = k_iter;
-        if (act && !T.big) {
+        if (act) {
           const Problem& P = L.probs[T.p];
           // 16-byte-aligned windows of every array the tile needs
           const int32_t eb = T.e0 & ~3, ee = (T.e1 + 3) & ~3;
@@ -776,8 +780,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
     // ------------------------------------------------------------ consumers
     // The CTA's tiles t_j = blockIdx.x + j*gridDim.x are visited in order by
     // every consumer warp: wait until tile j has landed, work on its own slots,
-    // arrive on the stage's "empty" barrier. A slot is a column, or a whole
-    // tile read from global memory. Slots are dealt
+    // arrive on the stage's "empty" barrier. A slot is a column. Slots are dealt
     // round-robin across tiles, so a warp that has nothing left in tile j moves
     // on to tile j+1 while the others finish. Because every warp visits every
     // tile, no warp can fall two rounds behind a stage, which keeps the parity
@@ -796,7 +799,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
       (void)mbar_try_wait(&S.full[stage], round & 1);  // completed phase: acquire for every lane
       Stage& st = S.st[stage];
       const Tile T = st.tile;
-      const int32_t nslots = T.big ? 1 : T.c1 - T.c0;
+      const int32_t nslots = T.c1 - T.c0;
       const int32_t k_iter = st.k_iter;
       const bool active = st.active != 0;
       // first local slot of this warp: global slot g with g % kConsumerWarps == warp
@@ -804,41 +807,10 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
       if (first < 0) first += kConsumerWarps;
       for (int32_t ls = first; ls < nslots; ls += kConsumerWarps) {
         if (active) {
-          if (!T.big) {
-            if (st.prob.lg32)
-              stage_column<true>(st, T, ls, k_iter, ws, lane);
-            else
-              stage_column<false>(st, T, ls, k_iter, ws, lane);
-          } else {
-            // one state too large for a stage: this warp reads its columns from global memory
-            const Problem& P = L.probs[T.p];
-            const bool pess = P.pessimistic != 0;
-            const uint64_t* __restrict__ Vin = P.V[(k_iter - 1) & 1];
-            uint64_t bestq = 0;
-            int32_t best = -1;
-            for (int32_t cc = T.c0; cc < T.c1; ++cc) {
-              const int32_t ca = __ldg(P.colptr + cc), ce = __ldg(P.colptr + cc + 1);
-              const int32_t h = P.hint ? P.hint[cc] : -1;
-              int32_t hout;
-              uint64_t q;
-              if (P.lg32) {
-                const Bounds<true> bd{P.lg32 + ca, 32 - __ldg(P.shift + cc)};
-                q = column_q<true>(P.rowval + ca, bd, ce - ca, __ldg(P.rem + cc), Vin, pess, ws, lane, h, &hout);
-              } else {
-                const Bounds<false> bd{P.lg + ca, 0};
-                q = column_q<false>(P.rowval + ca, bd, ce - ca, __ldg(P.rem + cc), Vin, pess, ws, lane, h, &hout);
-              }
-              if (lane == 0 && P.hint && hout != h) P.hint[cc] = hout;
-              if (best < 0 || (P.maximize ? q > bestq : q < bestq)) {
-                bestq = q;
-                best = cc - T.c0;
-              }
-            }
-            if (lane == 0) {
-              st.q[0] = bestq;
-              st.q[1] = (unsigned long long)(long long)best;
-            }
-          }
+          if (st.prob.lg32)
+            stage_column<true>(st, T, ls, k_iter, ws, lane);
+          else
+            stage_column<false>(st, T, ls, k_iter, ws, lane);
         }
         // count the slot; the warp that completes the tile finishes its states
         unsigned prev = 0;
@@ -851,22 +823,14 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
         if (prev + 1 == (unsigned)nslots) {
           __threadfence_block();
           if (active) {
-            if (T.big) {
-              const Problem& P = L.probs[T.p];
-              const uint64_t bq = st.q[0];
-              const int32_t bb = (int32_t)(long long)st.q[1];
-              tile_epilogue(L, P, T, k_iter, lane, [&](int32_t s) { return P.fixed[s]; },
-                            [&](int32_t, uint64_t* q, int32_t* b) { *q = bq; *b = bb; });
-            } else {
-              const Problem& P = st.prob;
-              const int32_t sb = T.s0 & ~3;
-              tile_epilogue(L, P, T, k_iter, lane,
-                            [&](int32_t s) { return st.fixed[st.fixed_off + (s - T.s0)]; },
-                            [&](int32_t s, uint64_t* bq, int32_t* bb) {
-                              const int32_t jb = st.sptr[s - sb], je = st.sptr[s + 1 - sb];
-                              best_action(P, jb, je, [&](int32_t jj) { return st.q[jj - T.c0]; }, bq, bb);
-                            });
-            }
+            const Problem& P = st.prob;
+            const int32_t sb = T.s0 & ~3;
+            tile_epilogue(L, P, T, k_iter, lane,
+                          [&](int32_t s) { return st.fixed[st.fixed_off + (s - T.s0)]; },
+                          [&](int32_t s, uint64_t* bq, int32_t* bb) {
+                            const int32_t jb = st.sptr[s - sb], je = st.sptr[s + 1 - sb];
+                            best_action(P, jb, je, [&](int32_t jj) { return st.q[jj - T.c0]; }, bq, bb);
+                          });
           }
           __syncwarp();
           if (lane == 0) st.done = 0;
@@ -879,15 +843,20 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
 
   }
 
-  // The last CTA to finish advances every running problem's iteration state.
+  end_of_launch(L, &S.is_last);
+}
+
+// The last CTA of the launch (of either step kernel) advances every running
+// problem's iteration state and resets the launch counters.
+__device__ void end_of_launch(const StepLaunch& L, int* is_last) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int prev = atomicAdd(&L.ctl->finished, 1u);
-    S.is_last = (prev == gridDim.x - 1);
+    *is_last = (prev == (unsigned)L.grid_total - 1u);
   }
   __syncthreads();
-  if (!S.is_last) return;
+  if (!*is_last) return;
   __threadfence();
   for (int q = threadIdx.x; q < L.count; q += blockDim.x) {
     IterState* it = &L.its[q];
@@ -916,34 +885,485 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
       it->k_final = kq;
     }
   }
-  if (threadIdx.x == 0) L.ctl->finished = 0;
+  if (threadIdx.x == 0) {
+    L.ctl->finished = 0;
+    L.ctl->wide_next = 0;
+  }
+}
+
+// ---------------------------------------------------------------- wide states
+//
+// A state whose entries do not fit one stage, or that has a column of kWideCol
+// entries or more, is handled by the 4 warps of a CTA together: thread t takes
+// entries t, t + 128, ... of each column, and the warps' partial sums are
+// combined through shared memory between __syncthreads (no spin waits). Every
+// sum is the same multiset of exact integer terms as in the one-warp routines
+// (and candidate ties are ordered by entry index, as there), so a wide state
+// gets the same result, to the bit, as it would in a tile.
+
+constexpr int kWideWarps = 4;
+constexpr int kWideThreads = 32 * kWideWarps;
+
+struct WideShared {
+  unsigned long long r[4][kWideWarps];  // per-warp partials
+  int32_t ri[kWideWarps];
+  int32_t rh[kWideWarps];
+  unsigned int hl[kBins];               // histogram as in WarpScratch
+  unsigned int hh[kBins];
+  unsigned int hc[kBins];
+  unsigned int hsat[2];
+  unsigned long long ck[32];            // candidates: key, gap, entry
+  unsigned long long cg[32];
+  int32_t ci[32];
+  unsigned int ncand;
+  int32_t first_cand;
+  unsigned long long bc[4];             // values broadcast by warp 0
+  int32_t bci[2];
+};
+
+// Block sums of per-thread values: a mod 2^64, f and g saturating (inputs as for
+// warp_sum_sat). Two barriers: the partials are published, then free again.
+__device__ __forceinline__ void block_sum3(WideShared& W, int warp, int lane, uint64_t& a, uint64_t& f,
+                                           uint64_t& g) {
+  a = warp_sum_u64(a);
+  f = warp_sum_sat(f);
+  g = warp_sum_sat(g);
+  if (lane == 0) {
+    W.r[0][warp] = a;
+    W.r[1][warp] = f;
+    W.r[2][warp] = g;
+  }
+  __syncthreads();
+  a = f = g = 0;
+  for (int w = 0; w < kWideWarps; ++w) {
+    a += W.r[0][w];
+    f = sat_add(f, W.r[1][w]);
+    g = sat_add(g, W.r[2][w]);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void block_minmax(WideShared& W, int warp, int lane, uint64_t& mn, uint64_t& mx) {
+  mn = warp_min_u64(mn);
+  mx = warp_max_u64(mx);
+  if (lane == 0) {
+    W.r[0][warp] = mn;
+    W.r[1][warp] = mx;
+  }
+  __syncthreads();
+  mn = ~0ull;
+  mx = 0;
+  for (int w = 0; w < kWideWarps; ++w) {
+    mn = W.r[0][w] < mn ? W.r[0][w] : mn;
+    mx = W.r[1][w] > mx ? W.r[1][w] : mx;
+  }
+  __syncthreads();
+}
+
+// Neighbour check of column_neighbor, block-wide.
+template <bool f32>
+__device__ bool wide_neighbor(const int32_t* __restrict__ rows, const Bounds<f32> lg, int32_t k, uint64_t rem,
+                              const uint64_t* __restrict__ V, bool pess, uint64_t vk, uint64_t acc, uint64_t flt,
+                              uint64_t geq, uint64_t* q, int32_t* hint_out, WideShared& W) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool down = flt >= rem;
+  if (down && flt >= kOne) return false;
+  const uint64_t kap = pess ? vk : kOne - vk;
+  uint64_t best = 0, gs = 0, ds = 0, dk = 0;
+  bool have = false;
+  int32_t bi = -1;
+  for (int idx = tid; idx < k; idx += kWideThreads) {
+    const uint64_t v = __ldg(V + rows[idx]);
+    const uint64_t key = pess ? v : kOne - v;
+    const ulonglong2 b = lg[idx];
+    const uint64_t d = __umul64hi(v, b.x + b.y) - __umul64hi(v, b.x);
+    const bool side = down ? key < kap : key > kap;
+    if (side) {
+      if (!have || (down ? key > best : key < best)) {
+        best = key;
+        gs = b.y;
+        ds = d;
+        bi = idx;
+        have = true;
+      } else if (key == best) {
+        gs = sat_add(gs, b.y);
+        ds += d;
+        bi = idx < bi ? idx : bi;
+      }
+    } else if (!down && key == kap) {
+      dk += d;
+    }
+  }
+  const bool any = __any_sync(kFull, have);
+  const uint64_t tw = down ? warp_max_u64(have ? best : 0ull) : warp_min_u64(have ? best : ~0ull);
+  const bool mine = have && best == tw;
+  const uint64_t Gw = warp_sum_sat(mine ? gs : 0ull);
+  const uint64_t Dw = warp_sum_u64(mine ? ds : 0ull);
+  const uint64_t DKw = warp_sum_u64(dk);
+  const int32_t hw = __reduce_min_sync(kFull, mine ? (unsigned)bi : 0x7fffffffu);
+  if (lane == 0) {
+    W.rh[warp] = any ? 1 : 0;
+    W.r[0][warp] = tw;
+    W.r[1][warp] = Gw;
+    W.r[2][warp] = Dw;
+    W.r[3][warp] = DKw;
+    W.ri[warp] = hw;
+  }
+  __syncthreads();
+  bool anyb = false;
+  uint64_t t = down ? 0ull : ~0ull;
+  for (int w = 0; w < kWideWarps; ++w)
+    if (W.rh[w]) {
+      anyb = true;
+      t = down ? (W.r[0][w] > t ? W.r[0][w] : t) : (W.r[0][w] < t ? W.r[0][w] : t);
+    }
+  uint64_t G = 0, D = 0, DK = 0;
+  int32_t h = 0x7fffffff;
+  for (int w = 0; w < kWideWarps; ++w) {
+    DK += W.r[3][w];
+    if (W.rh[w] && W.r[0][w] == t) {
+      G = sat_add(G, W.r[1][w]);
+      D += W.r[2][w];
+      h = W.ri[w] < h ? W.ri[w] : h;
+    }
+  }
+  __syncthreads();
+  if (!anyb) return false;
+  const uint64_t vt = pess ? t : kOne - t;
+  if (down) {
+    const uint64_t fl = flt - G;
+    if (fl >= rem) return false;
+    *q = acc - D + __umul64hi(vt, rem - fl);
+  } else {
+    const uint64_t fl = flt + geq;
+    if (sat_add(fl, G) < rem) return false;
+    *q = acc + DK + __umul64hi(vt, rem - fl);
+  }
+  *hint_out = h;
+  return true;
+}
+
+// Threshold search of column_search, block-wide.
+template <bool f32>
+__device__ uint64_t wide_search(const int32_t* __restrict__ rows, const Bounds<f32> lg, int32_t k, uint64_t rem,
+                                const uint64_t* __restrict__ V, bool pess, int32_t* found, WideShared& W) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  auto key_of = [&](int idx) -> uint64_t {
+    const uint64_t v = __ldg(V + rows[idx]);
+    return pess ? v : (kOne - v);
+  };
+  uint64_t cmin = ~0ull, cmax = 0;
+  for (int idx = tid; idx < k; idx += kWideThreads) {
+    const uint64_t key = key_of(idx);
+    cmin = key < cmin ? key : cmin;
+    cmax = key > cmax ? key : cmax;
+  }
+  block_minmax(W, warp, lane, cmin, cmax);
+  uint64_t lo = 0, hi = kOne, fb = 0;
+  bool all_below = false, uniform = false;
+  for (int round = 0; round < 12; ++round) {
+    if (cmin > cmax) {
+      all_below = true;
+      break;
+    }
+    if (cmin == cmax) {
+      lo = hi = cmin;
+      uniform = true;
+      break;
+    }
+    const int bits = 64 - __clzll((long long)(cmax - cmin));
+    const int shift = bits > 6 ? bits - 6 : 0;
+    if (tid < kBins) {
+      W.hl[tid] = 0;
+      W.hh[tid] = 0;
+      W.hc[tid] = 0;
+    }
+    if (tid == 0) W.hsat[0] = W.hsat[1] = 0;
+    __syncthreads();
+    for (int idx = tid; idx < k; idx += kWideThreads) {
+      const uint64_t key = key_of(idx);
+      if (key >= lo && key <= hi) {
+        const int b = (int)((key - cmin) >> shift);
+        const uint64_t g = lg[idx].y < rem ? lg[idx].y : rem;
+        const unsigned gl = (unsigned)g;
+        const unsigned old = atomicAdd(&W.hl[b], gl);
+        const unsigned up = (unsigned)(g >> 32) + ((old + gl) < old ? 1u : 0u);
+        if (up) {
+          const unsigned oh = atomicAdd(&W.hh[b], up);
+          if (oh + up < oh) atomicOr(&W.hsat[b >> 5], 1u << (b & 31));
+        }
+        atomicAdd(&W.hc[b], 1u);
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned sat = W.hsat[lane >> 4];
+      const uint64_t h0 = ((sat >> ((2 * lane) & 31)) & 1u) ? ~0ull
+                                                            : (((uint64_t)W.hh[2 * lane] << 32) | W.hl[2 * lane]);
+      const uint64_t h1 = ((sat >> ((2 * lane + 1) & 31)) & 1u)
+                              ? ~0ull
+                              : (((uint64_t)W.hh[2 * lane + 1] << 32) | W.hl[2 * lane + 1]);
+      const uint64_t ex = warp_excl_scan_sat(sat_add(h0, h1), lane);
+      const uint64_t i0 = sat_add(sat_add(fb, ex), h0), i1 = sat_add(i0, h1);
+      const unsigned cross = __ballot_sync(kFull, i1 >= rem);
+      if (cross == 0) {
+        if (lane == 0) W.bci[0] = -1;
+      } else {
+        const int L = __ffs(cross) - 1;
+        const bool first = i0 >= rem;
+        const int b = __shfl_sync(kFull, first ? 2 * lane : 2 * lane + 1, L);
+        const uint64_t f2 = __shfl_sync(kFull, first ? sat_add(fb, ex) : i0, L);
+        if (lane == 0) {
+          W.bci[0] = b;
+          W.bci[1] = (int32_t)W.hc[b];
+          W.bc[0] = f2;
+        }
+      }
+    }
+    __syncthreads();
+    const int b = W.bci[0];
+    const unsigned cnt = (unsigned)W.bci[1];
+    const uint64_t f2 = W.bc[0];
+    __syncthreads();
+    if (b < 0) {  // first round only: the gaps cannot absorb rem
+      all_below = true;
+      break;
+    }
+    fb = f2;
+    lo = cmin + ((uint64_t)b << shift);
+    const uint64_t top = lo + ((1ull << shift) - 1ull);
+    hi = top < cmax ? top : cmax;
+    if (cnt <= 32) break;
+    uint64_t a = ~0ull, z = 0;
+    for (int idx = tid; idx < k; idx += kWideThreads) {
+      const uint64_t key = key_of(idx);
+      if (key >= lo && key <= hi) {
+        a = key < a ? key : a;
+        z = key > z ? key : z;
+      }
+    }
+    block_minmax(W, warp, lane, a, z);
+    cmin = a;
+    cmax = z;
+  }
+  // final pass
+  if (tid == 0) {
+    W.ncand = 0;
+    W.first_cand = 0x7fffffff;
+  }
+  __syncthreads();
+  uint64_t acc = 0, gsum = 0, unused = 0;
+  for (int idx = tid; idx < k; idx += kWideThreads) {
+    const uint64_t key = key_of(idx);
+    const ulonglong2 b = lg[idx];
+    const bool below = all_below || key < lo;
+    const bool cand = !all_below && key >= lo && key <= hi;
+    acc += __umul64hi(pess ? key : (kOne - key), below ? b.x + b.y : b.x);
+    if (cand) {
+      atomicMin(&W.first_cand, idx);
+      const uint64_t g = b.y < rem ? b.y : rem;
+      if (uniform) {
+        gsum = sat_add(gsum, g);
+      } else {
+        const unsigned at = atomicAdd(&W.ncand, 1u);
+        if (at < 32) {
+          W.ck[at] = key;
+          W.cg[at] = g;
+          W.ci[at] = idx;
+        }
+      }
+    }
+  }
+  block_sum3(W, warp, lane, acc, gsum, unused);
+  if (all_below) {
+    *found = -1;
+    return acc;
+  }
+  const uint64_t r2 = rem - fb;
+  if (uniform) {
+    *found = W.first_cand;
+    return acc + __umul64hi(pess ? lo : (kOne - lo), gsum < r2 ? gsum : r2);
+  }
+  // resolve the <= 32 candidates in (key, entry) order, as the one-warp search does
+  if (warp == 0) {
+    const unsigned pos = W.ncand < 32u ? W.ncand : 32u;
+    uint64_t extra = 0;
+    int thr = -1;
+    if (lane < (int)pos) {
+      const uint64_t ki = W.ck[lane], gi = W.cg[lane];
+      const int32_t ii = W.ci[lane];
+      uint64_t before = 0;
+      for (unsigned j = 0; j < pos; ++j) {
+        const uint64_t kj = W.ck[j];
+        if (kj < ki || (kj == ki && W.ci[j] < ii)) before = sat_add(before, W.cg[j]);
+      }
+      const uint64_t left = r2 > before ? r2 - before : 0;
+      extra = __umul64hi(pess ? ki : (kOne - ki), gi < left ? gi : left);
+      if (left > 0 && left <= gi) thr = ii;
+    }
+    extra = warp_sum_u64(extra);
+    const int32_t t = __reduce_min_sync(kFull, thr >= 0 ? (unsigned)thr : 0x7fffffffu);
+    if (lane == 0) {
+      W.bc[1] = extra;
+      W.bci[0] = t == 0x7fffffff ? -1 : t;
+    }
+  }
+  __syncthreads();
+  const uint64_t q = acc + W.bc[1];
+  *found = W.bci[0];
+  __syncthreads();
+  return q;
+}
+
+// One column of a wide state: warm start, neighbour check, search (the same
+// sequence and hint encoding as column_q).
+template <bool f32>
+__device__ uint64_t wide_column_q(const int32_t* __restrict__ rows, const Bounds<f32> lg, int32_t k,
+                                  uint64_t rem_word, const uint64_t* __restrict__ V, bool pess, int32_t hint,
+                                  int32_t* hint_out, WideShared& W) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint64_t rem = rem_of(rem_word);
+  const bool moving = hint <= -2;
+  const int32_t entry = moving ? -2 - hint : hint;
+  if (rem == 0) {
+    uint64_t a = 0, f = 0, g = 0;
+    for (int idx = tid; idx < k; idx += kWideThreads) a += __umul64hi(__ldg(V + rows[idx]), lg[idx].x);
+    block_sum3(W, warp, lane, a, f, g);
+    *hint_out = entry;
+    return a;
+  }
+  if (entry >= 0 && entry < k) {
+    const uint64_t vk = __ldg(V + rows[entry]);
+    uint64_t acc = 0, flt = 0, geq = 0;
+    uint32_t fc = 0, gc = 0;
+    for (int idx = tid; idx < k; idx += kWideThreads) {
+      const uint64_t v = __ldg(V + rows[idx]);
+      const ulonglong2 b = lg[idx];
+      const bool below = pess ? (v < vk) : (v > vk);
+      acc += __umul64hi(v, b.x + (below ? b.y : 0ull));
+      const uint64_t gb = below ? b.y : 0ull, ge = v == vk ? b.y : 0ull;
+      flt += gb;
+      fc += flt < gb ? 1u : 0u;
+      geq += ge;
+      gc += geq < ge ? 1u : 0u;
+    }
+    flt = fc ? ~0ull : flt;
+    geq = gc ? ~0ull : geq;
+    block_sum3(W, warp, lane, acc, flt, geq);
+    if (flt < rem && rem - flt <= geq) {
+      *hint_out = entry;
+      return acc + __umul64hi(vk, rem - flt);
+    }
+    uint64_t q;
+    int32_t h;
+    if (!moving && wide_neighbor<f32>(rows, lg, k, rem, V, pess, vk, acc, flt, geq, &q, &h, W)) {
+      *hint_out = h;
+      return q;
+    }
+  }
+  int32_t found;
+  const uint64_t q = wide_search<f32>(rows, lg, k, rem, V, pess, &found, W);
+  *hint_out = found >= 0 ? -2 - found : -1;
+  return q;
+}
+
+// One Bellman step of the wide states: each CTA takes the next wide state until
+// none is left. It runs beside bellman_step_kernel (on a second stream, in the
+// room one persistent tiled CTA leaves on each SM) or before it: both read
+// V_{k-1} and write disjoint states of V_k, and whichever CTA of the two
+// kernels finishes last advances the iteration state.
+__global__ void __launch_bounds__(kWideThreads, 512 / kWideThreads) bellman_wide_kernel(StepLaunch L) {
+  __shared__ WideShared W;
+  __shared__ int take;
+  __shared__ int is_last;
+  for (;;) {
+    if (threadIdx.x == 0) take = (int)atomicAdd(&L.ctl->wide_next, 1u);
+    __syncthreads();
+    const int32_t w = take;
+    __syncthreads();
+    if (w >= L.n_wide) break;
+    const int2 ps = L.wide[w];
+    const Problem& P = L.probs[ps.x];
+    int32_t k_iter;
+    if (!problem_active(L, ps.x, &k_iter)) continue;
+    const int32_t s = ps.y;
+    const uint8_t fx = P.fixed[s];
+    const uint64_t* __restrict__ Vin = P.V[(k_iter - 1) & 1];
+    uint64_t* __restrict__ Vout = P.V[k_iter & 1];
+    uint64_t vnew;
+    int32_t best = -1;
+    if (fx == 1) {
+      vnew = kOne;
+    } else if (fx == 2) {
+      vnew = 0;
+    } else {
+      const bool pess = P.pessimistic != 0;
+      const int32_t c0 = __ldg(P.stateptr + s), c1 = __ldg(P.stateptr + s + 1);
+      uint64_t bestq = 0;
+      for (int32_t c = c0; c < c1; ++c) {
+        const int32_t ca = __ldg(P.colptr + c), ce = __ldg(P.colptr + c + 1);
+        const int32_t h = P.hint ? P.hint[c] : -1;
+        int32_t hout;
+        uint64_t q;
+        if (P.lg32)
+          q = wide_column_q<true>(P.rowval + ca, Bounds<true>{P.lg32 + ca, 32 - __ldg(P.shift + c)}, ce - ca,
+                                  __ldg(P.rem + c), Vin, pess, h, &hout, W);
+        else
+          q = wide_column_q<false>(P.rowval + ca, Bounds<false>{P.lg + ca, 0}, ce - ca, __ldg(P.rem + c), Vin, pess,
+                                   h, &hout, W);
+        if (threadIdx.x == 0 && P.hint && hout != h) P.hint[c] = hout;
+        if (best < 0 || (P.maximize ? q > bestq : q < bestq)) {
+          bestq = q;
+          best = c - c0;
+        }
+      }
+      if (P.property == kPropReward) {
+        const int64_t tt = (int64_t)(__umul64hi(P.gamma_fix, bestq) << 1);
+        int64_t wv = P.rbias[s] + tt;
+        wv = wv < 0 ? 0 : (wv > (int64_t)(kOne >> 1) ? (int64_t)(kOne >> 1) : wv);
+        vnew = (uint64_t)wv << 1;
+      } else {
+        vnew = bestq >= (kOne >> 1) ? kOne : (bestq << 1);
+      }
+    }
+    if (threadIdx.x == 0) {
+      unsigned long long dmax = 0;
+      finish_state(P, s, k_iter, vnew, best, Vin, Vout, dmax);
+      if (P.infinite && dmax) atomicMax(&L.its[ps.x].resmax, dmax);
+    }
+  }
+  end_of_launch(L, &is_last);
 }
 
 }  // namespace
 
-void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out) {
+void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out, std::vector<int32_t>& wide) {
   const std::vector<int32_t>& sp = m->h_stateptr;
   const std::vector<int32_t>& cp = m->h_colptr;
-  const int32_t n = m->own1;  // tiles cover the owned states only
+  const int32_t n = m->own1;  // owned states only
+  auto is_wide = [&](int32_t s) {
+    if (cp[sp[s + 1]] - cp[sp[s]] > kTileEntries || sp[s + 1] - sp[s] > kTileCols) return true;
+    for (int32_t c = sp[s]; c < sp[s + 1]; ++c)
+      if (cp[c + 1] - cp[c] >= kWideCol) return true;
+    return false;
+  };
   int32_t s = m->own0;
   while (s < n) {
+    if (is_wide(s)) {
+      wide.push_back(s);
+      ++s;
+      continue;
+    }
     Tile T;
     T.p = problem;
     T.s0 = s;
     T.c0 = sp[s];
     T.e0 = cp[sp[s]];
-    const int32_t ent = cp[sp[s + 1]] - T.e0;
-    if (ent > kTileEntries || sp[s + 1] - sp[s] > kTileCols) {
-      T.s1 = s + 1;
-      T.big = 1;
-    } else {
-      int32_t t = s + 1;
-      while (t < n && cp[sp[t + 1]] - T.e0 <= kTileEntries && sp[t + 1] - T.c0 <= kTileCols &&
-             t + 1 - s <= kTileStates)
-        ++t;
-      T.s1 = t;
-      T.big = 0;
-    }
+    int32_t t = s + 1;
+    while (t < n && !is_wide(t) && cp[sp[t + 1]] - T.e0 <= kTileEntries && sp[t + 1] - T.c0 <= kTileCols &&
+           t + 1 - s <= kTileStates)
+      ++t;
+    T.s1 = t;
     T.c1 = sp[T.s1];
     T.e1 = cp[T.c1];
     out.push_back(T);
@@ -960,17 +1380,47 @@ int bellman_grid(int, int) {
   return sms;  // persistent: one CTA per SM
 }
 
-cudaError_t launch_bellman_step(const StepLaunch& L, int grid, cudaStream_t st) {
+cudaError_t launch_bellman_step(const StepLaunch& L0, int grid, cudaStream_t st, const SideStream* side) {
   static int configured[64] = {0};
+  static int wide_blocks[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !configured[dev]) {
-    const cudaError_t e = cudaFuncSetAttribute(bellman_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)sizeof(Smem));
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!configured[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(bellman_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(Smem));
     if (e != cudaSuccess) return e;
+    int per_sm = 1, sms = 152;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_wide_kernel, kWideThreads, 0);
+    if (e != cudaSuccess) return e;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    wide_blocks[dev] = std::max(1, per_sm) * sms;
     configured[dev] = 1;
   }
-  bellman_step_kernel<<<grid, kBlockThreads, sizeof(Smem), st>>>(L);
+  StepLaunch L = L0;
+  const int mg = L.n_tiles > 0 ? grid : 1;  // one CTA still takes part in the end-of-launch ticket
+  const int wg = L.n_wide > 0 ? std::min(L.n_wide, wide_blocks[dev]) : 0;
+  L.grid_total = mg + wg;
+  cudaError_t e = cudaSuccess;
+  if (wg > 0 && side && side->stream && L.n_tiles > 0) {
+    // fork / join: the tiled kernel is issued first so that its persistent CTAs
+    // hold the SMs; wide CTAs run in the room left beside them
+    e = cudaEventRecord(side->fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side->stream, side->fork, 0);
+    if (e != cudaSuccess) return e;
+    bellman_step_kernel<<<mg, kBlockThreads, sizeof(Smem), st>>>(L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    bellman_wide_kernel<<<wg, kWideThreads, 0, side->stream>>>(L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = cudaEventRecord(side->join, side->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, side->join, 0);
+    return e;
+  }
+  if (wg > 0) {
+    bellman_wide_kernel<<<wg, kWideThreads, 0, st>>>(L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  bellman_step_kernel<<<mg, kBlockThreads, sizeof(Smem), st>>>(L);
   return cudaGetLastError();
 }
 

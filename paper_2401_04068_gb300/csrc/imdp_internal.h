@@ -33,17 +33,18 @@ enum : int32_t { kPropReach = 0, kPropReachAvoid = 1, kPropReward = 2 };
 
 // A tile is a run of consecutive states of one problem whose entries are
 // streamed into shared memory by one bulk copy per array (state-aligned, so a
-// CTA finishes the opt over actions on its own). A state with more than
-// kTileEntries entries forms a tile of its own that is read from global memory.
+// CTA finishes the opt over actions on its own). A state whose entries do not
+// fit one stage, or that has a column of kWideCol entries or more, is "wide": a
+// whole CTA works on it (bellman_wide_kernel) and it belongs to no tile.
 constexpr int kTileEntries = 3072;  // entries per tile (rowval 12 KB + bounds 48 KB + keys 24 KB)
 constexpr int kTileCols = 256;      // columns per tile
 constexpr int kTileStates = 256;    // states per tile
+constexpr int kWideCol = 1280;      // columns this long make their state wide
 struct Tile {
   int32_t p;      // problem
   int32_t s0, s1; // states [s0, s1) of that problem
   int32_t c0, c1; // columns [c0, c1)
   int32_t e0, e1; // entries [e0, e1)
-  int32_t big;    // 1: entries exceed a stage, consumers read global memory
 };
 
 // Device-resident model (the "IntervalMDP.cu(problem)" transfer of Sec. 3.2,
@@ -70,6 +71,9 @@ struct DevModel {
   std::vector<Tile> h_tiles;        // tile plan of this model (problem index 0)
   Tile* tiles = nullptr;            // device copy of h_tiles
   int32_t n_tiles = 0;
+  std::vector<int32_t> h_wide;      // wide states (in no tile)
+  int2* wide = nullptr;             // device copy as (problem 0, state)
+  int32_t n_wide = 0;
 };
 
 
@@ -110,8 +114,28 @@ struct IterState {
 };
 
 struct StepControl {
-  unsigned int finished;  // blocks finished in the running launch
-  unsigned int error;     // nonzero: a bounded wait inside the kernel gave up
+  unsigned int finished;   // CTAs (of both step kernels) finished in the running launch
+  unsigned int error;      // nonzero: a bounded wait inside the kernel gave up
+  unsigned int wide_next;  // next wide state to take in the running launch
+};
+
+// Second stream on which the wide-state kernel runs beside the tiled one.
+struct SideStream {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaError_t create() {
+    cudaError_t e = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    return e;
+  }
+  void destroy() {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (stream) cudaStreamDestroy(stream);
+    stream = nullptr;
+    fork = join = nullptr;
+  }
 };
 
 struct StepLaunch {
@@ -125,15 +149,22 @@ struct StepLaunch {
   int32_t col_class;  // unused by the tiled kernel (kept for the launch helpers)
   const Tile* tiles;
   int32_t n_tiles;
-  int32_t _pad2;
+  int32_t n_wide;
+  const int2* wide;  // (problem, state) of every wide state
+  int32_t grid_total;  // CTAs of both step kernels in this launch (set by the launcher)
+  int32_t _pad3;
 };
 
 // bellman.cu
-cudaError_t launch_bellman_step(const StepLaunch& L, int grid, cudaStream_t st);
+// One Bellman iteration: the wide-state kernel (on `side`, beside the tiled one,
+// when given) and the tiled kernel; the last CTA of the two advances the
+// iteration state.
+cudaError_t launch_bellman_step(const StepLaunch& L, int grid, cudaStream_t st, const SideStream* side = nullptr);
 int choose_col_class(int32_t max_col);
 int bellman_grid(int total_states, int col_class);
-// Tile plan for one problem's model (host), appended to `out`.
-void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out);
+// Tile plan for one problem's model (host): tiles appended to `out`, wide
+// states (no tile) appended to `wide`.
+void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out, std::vector<int32_t>& wide);
 
 // model.cu
 imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, const int32_t* stateptr,
@@ -172,6 +203,9 @@ struct Session {
   StepControl* ctl = nullptr;
   Tile* tiles = nullptr;
   int32_t n_tiles = 0;
+  int2* wide = nullptr;
+  int32_t n_wide = 0;
+  SideStream side;  // created when the session has both tiles and wide states
   StepLaunch L{};
   int grid = 1;
   cudaGraphExec_t graph = nullptr;

@@ -167,6 +167,7 @@ void model_destroy(DevModel* m) {
   cudaFree(m->lg);
   cudaFree(m->rem);
   cudaFree(m->tiles);
+  cudaFree(m->wide);
   cudaFree(m->lg32);
   cudaFree(m->shift);
   delete m;
@@ -321,16 +322,25 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
   }
   m->h_stateptr = std::move(hs);
   m->h_colptr = std::move(hc);
-  plan_tiles(m, 0, m->h_tiles);
+  plan_tiles(m, 0, m->h_tiles, m->h_wide);
   m->n_tiles = (int32_t)m->h_tiles.size();
-  if (cudaMalloc(&m->tiles, sizeof(Tile) * m->h_tiles.size()) != cudaSuccess) {
+  m->n_wide = (int32_t)m->h_wide.size();
+  std::vector<int2> wide2(m->h_wide.size());
+  for (size_t i = 0; i < wide2.size(); ++i) wide2[i] = make_int2(0, m->h_wide[i]);
+  if (cudaMalloc(&m->tiles, sizeof(Tile) * std::max<size_t>(m->h_tiles.size(), 1)) != cudaSuccess ||
+      cudaMalloc(&m->wide, sizeof(int2) * std::max<size_t>(wide2.size(), 1)) != cudaSuccess) {
     cudaGetLastError();
     model_destroy(m);
     set_error("device allocation failed for the tile plan");
     return IMDP_ENOMEM;
   }
   m->bytes += sizeof(Tile) * m->h_tiles.size();
-  e = cudaMemcpyAsync(m->tiles, m->h_tiles.data(), sizeof(Tile) * m->h_tiles.size(), cudaMemcpyHostToDevice, st);
+  m->bytes += sizeof(int2) * wide2.size();
+  e = cudaSuccess;
+  if (!m->h_tiles.empty())
+    e = cudaMemcpyAsync(m->tiles, m->h_tiles.data(), sizeof(Tile) * m->h_tiles.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !wide2.empty())
+    e = cudaMemcpyAsync(m->wide, wide2.data(), sizeof(int2) * wide2.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { model_destroy(m); return cuda_status(e, "upload tile plan"); }
   *out = m;

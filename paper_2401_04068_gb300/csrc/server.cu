@@ -153,6 +153,8 @@ struct Server {
     cudaFree(d_ctl);
     cudaFree(d_base);
     cudaFree(d_tiles);
+    cudaFree(d_wide);
+    side.destroy();
     for (auto& kv : all) delete kv.second;
   }
 
@@ -251,12 +253,25 @@ struct Server {
 
   imdp_status upload_tables(int32_t count) {
     std::vector<Tile> tiles;
+    std::vector<int2> wide;
     for (int32_t s = 0; s < count; ++s) {
       Request* r = slots[s];
       if (!r) continue;
       const size_t at = tiles.size();
       tiles.insert(tiles.end(), r->model->h_tiles.begin(), r->model->h_tiles.end());
       for (size_t t = at; t < tiles.size(); ++t) tiles[t].p = s;
+      for (int32_t st : r->model->h_wide) wide.push_back(make_int2(s, st));
+    }
+    if (wide.size() > wide_cap) {
+      cudaFree(d_wide);
+      wide_cap = std::max(wide.size(), wide_cap * 2);
+      if (cudaMalloc(&d_wide, sizeof(int2) * wide_cap) != cudaSuccess) {
+        cudaGetLastError();
+        d_wide = nullptr;
+        wide_cap = 0;
+        set_error("server: wide-state table allocation failed");
+        return IMDP_ENOMEM;
+      }
     }
     if (tiles.size() > tile_cap) {
       cudaFree(d_tiles);
@@ -272,15 +287,22 @@ struct Server {
     cudaError_t e = cudaSuccess;
     if (!tiles.empty())
       e = cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && !wide.empty())
+      e = cudaMemcpyAsync(d_wide, wide.data(), sizeof(int2) * wide.size(), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_probs, probs_h.data(), sizeof(Problem) * count, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_status(e, "server tables");
     n_tiles = (int32_t)tiles.size();
+    n_wide = (int32_t)wide.size();
     return IMDP_OK;
   }
 
   int32_t n_tiles = 0;
+  int32_t n_wide = 0;
+  SideStream side;
+  int2* d_wide = nullptr;
+  size_t wide_cap = 0;
 
   void retire(Request* r, const IterState& it) {
     const DevModel* m = r->model;
@@ -368,9 +390,11 @@ struct Server {
       L.col_class = 1;
       L.tiles = d_tiles;
       L.n_tiles = n_tiles;
+      L.wide = d_wide;
+      L.n_wide = n_wide;
       const int grid = bellman_grid(0, 1);
       cudaError_t e = cudaSuccess;
-      for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = launch_bellman_step(L, grid, stream);
+      for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = launch_bellman_step(L, grid, stream, &side);
       its.resize(count);
       StepControl c{};
       if (e == cudaSuccess) e = cudaMemcpyAsync(its.data(), d_its, sizeof(IterState) * count, cudaMemcpyDeviceToHost, stream);
@@ -428,6 +452,7 @@ imdp_status imdp_server_create(size_t hbm_budget, imdp_server** out) {
   S->slots.assign(S->max_active, nullptr);
   S->probs_h.assign(S->max_active, Problem{});
   cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = S->side.create();
   if (e == cudaSuccess) e = cudaMalloc(&S->base, S->arena.size());
   if (e == cudaSuccess) e = cudaMalloc(&S->d_probs, sizeof(Problem) * S->max_active);
   if (e == cudaSuccess) e = cudaMalloc(&S->d_its, sizeof(IterState) * S->max_active);

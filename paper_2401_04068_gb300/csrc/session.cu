@@ -112,6 +112,7 @@ imdp_status check_spec(const DevModel* m, const imdp_spec* sp) {
 
 Session::~Session() {
   if (graph) cudaGraphExecDestroy(graph);
+  side.destroy();
   for (void* p : allocs) cudaFree(p);
 }
 
@@ -161,13 +162,17 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   S->v_scale.assign(count, 1.0);
   S->w0.assign(count, nullptr);
   std::vector<Tile> tiles;
+  std::vector<int2> wide;
   for (int p = 0; p < count; ++p) {
     const size_t at = tiles.size();
     tiles.insert(tiles.end(), ms[p]->h_tiles.begin(), ms[p]->h_tiles.end());
     for (size_t t = at; t < tiles.size(); ++t) tiles[t].p = p;
+    for (int32_t s : ms[p]->h_wide) wide.push_back(make_int2(p, s));
   }
   S->n_tiles = (int32_t)tiles.size();
   S->tiles = S->alloc<Tile>(tiles.size());
+  S->n_wide = (int32_t)wide.size();
+  S->wide = S->alloc<int2>(wide.size());
   // each problem's hint block starts on a 16-byte boundary and is padded, so
   // the kernel's bulk copies of hint windows stay aligned and in bounds
   for (int p = 0; p < count; ++p) S->total_cols += (int64_t)padded_i32(ms[p]->n_cols);
@@ -178,7 +183,7 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   S->probs = S->alloc<Problem>(count);
   S->its = S->alloc<IterState>(count);
   S->ctl = S->alloc<StepControl>(1);
-  if (!S->hints || !S->tiles || !S->fixed || !S->V || !S->base || !S->probs || !S->its || !S->ctl) {
+  if (!S->hints || !S->wide || !S->tiles || !S->fixed || !S->V || !S->base || !S->probs || !S->its || !S->ctl) {
     delete S; set_error("device allocation failed (session)"); return IMDP_ENOMEM;
   }
   S->probs_h.resize(count);
@@ -250,7 +255,10 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   if (e == cudaSuccess) e = cudaMemcpyAsync(S->fixed, fixed.data(), total, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S->base, S->base_h.data(), sizeof(int32_t) * (count + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S->probs, S->probs_h.data(), sizeof(Problem) * count, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(S->tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !tiles.empty())
+    e = cudaMemcpyAsync(S->tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !wide.empty())
+    e = cudaMemcpyAsync(S->wide, wide.data(), sizeof(int2) * wide.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host staging vectors go out of scope
   if (e != cudaSuccess) { delete S; return cuda_status(e, "session setup"); }
   S->L.probs = S->probs;
@@ -263,6 +271,12 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   S->L.col_class = max_class;
   S->L.tiles = S->tiles;
   S->L.n_tiles = S->n_tiles;
+  S->L.wide = S->wide;
+  S->L.n_wide = S->n_wide;
+  if (S->n_wide > 0 && S->n_tiles > 0 && (e = S->side.create()) != cudaSuccess) {
+    delete S;
+    return cuda_status(e, "session side stream");
+  }
   S->grid = bellman_grid((int)total, max_class);
   imdp_status r = S->reset(st);
   if (r != IMDP_OK) { delete S; return r; }
@@ -298,7 +312,7 @@ imdp_status Session::step(int32_t n, cudaStream_t st) {
     if (!graph) {
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-      for (int i = 0; i < kGraphChunk && e == cudaSuccess; ++i) e = launch_bellman_step(L, grid, st);
+      for (int i = 0; i < kGraphChunk && e == cudaSuccess; ++i) e = launch_bellman_step(L, grid, st, &side);
       cudaError_t e2 = cudaStreamEndCapture(st, &g);
       if (e == cudaSuccess) e = e2;
       if (e == cudaSuccess) e = cudaGraphInstantiate(&graph, g, 0);
@@ -310,7 +324,7 @@ imdp_status Session::step(int32_t n, cudaStream_t st) {
     }
     for (; done + kGraphChunk <= n && e == cudaSuccess; done += kGraphChunk) e = cudaGraphLaunch(graph, st);
   }
-  for (; done < n && e == cudaSuccess; ++done) e = launch_bellman_step(L, grid, st);
+  for (; done < n && e == cudaSuccess; ++done) e = launch_bellman_step(L, grid, st, &side);
   if (e != cudaSuccess) return cuda_status(e, "bellman step");
   launches += n;
   launched_since_reset += n;

@@ -82,15 +82,53 @@ def test_lower_equals_upper_and_rem_zero():
 
 # --------------------------------------------------------------------------- column-size classes and ragged tails
 
-@pytest.mark.parametrize("k_mean", [3, 20, 45, 100, 200, 400, 700])
+@pytest.mark.parametrize("k_mean", [3, 20, 45, 100, 200, 400, 700, 1100, 2600])
 def test_banded_column_classes(k_mean):
-    # spans every register class (<=32, 64, 128, 256, 512 entries) and the
-    # streaming path (> 512), with ragged column lengths
-    n_dom = max(3 * k_mean, 60)
+    # short columns (many per tile), long ones (a few per tile), and columns of
+    # 1024 entries or more (their states run block-wide), with ragged lengths
+    n_dom = max(3 * k_mean, 60) if k_mean < 1000 else k_mean + 200  # oracle-sized
     m = banded_imdp(n_dom, 2, n_dom * 2 * (k_mean + 1) + 1, eps=0.08, seed=k_mean)
     model = _model(m)
     for pess, maxi in [(True, True), (False, False)]:
         _compare(m, model, horizon=15, reach=m.goal, pessimistic=pess, maximize=maxi)
+
+
+def test_wide_and_tiled_states_mixed():
+    # one model whose states alternate between short columns (tiles) and columns
+    # of >= 1024 entries or several long actions (wide states), batched with a
+    # small model; results against the oracle, batch against alone to the bit
+    rng = np.random.default_rng(77)
+    n = 1400
+    sp, cp, rv, lo, up = [0], [0], [], [], []
+    for s in range(n):
+        acts = 1 + (s % 3)
+        for a in range(acts):
+            k = int(rng.integers(1100, 1300)) if (s % 7 == 0 and a == 0) else int(rng.integers(3, 60))
+            dest = np.sort(rng.choice(n, size=k, replace=False))
+            p = rng.random(k) + 0.01
+            p /= p.sum()
+            l = p * (1 - 0.1 * rng.random(k))
+            u = np.minimum(1.0, p * (1 + 0.1 * rng.random(k)))
+            rv.extend(dest.tolist()), lo.extend(l.tolist()), up.extend(u.tolist())
+            cp.append(len(rv))
+        sp.append(len(cp) - 1)
+    from workloads import IMDPInput
+    goal = np.arange(100, 160, dtype=np.int32)
+    m = IMDPInput(n, np.array(sp, np.int32), np.array(cp, np.int32), np.array(rv, np.int32), np.array(lo),
+                  np.array(up), goal)
+    model = _model(m)
+    for pess, maxi in MODES:
+        _compare(m, model, horizon=12, reach=m.goal, pessimistic=pess, maximize=maxi)
+    small = random_imdp(30, max_actions=3, seed=78)
+    sm = _model(small)
+    specs = [g.make_spec(horizon=20, reach=m.goal), g.make_spec(horizon=20, reach=small.goal, pessimistic=False)]
+    outs = [np.zeros(m.n_states), np.zeros(small.n_states)]
+    ks = np.zeros(2, np.int32)
+    g.imdp_value_iteration_batch([model, sm], specs, outs, ks)
+    for mdl, spec, out, n_s in [(model, specs[0], outs[0], m.n_states), (sm, specs[1], outs[1], small.n_states)]:
+        alone = np.zeros(n_s)
+        g.imdp_value_iteration(mdl, spec, alone)
+        np.testing.assert_array_equal(out, alone)
 
 
 def test_reach_avoid():
