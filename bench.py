@@ -328,6 +328,9 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_peak_hbm()
     alg_bytes = algorithmic_bytes_per_iteration(m, args.dtype)
     launch_ms = kernel_ms / (args.steps * args.horizon)
+    n_tiles, n_wide, wide_entries = g.imdp_model_plan(model)
+    wide_share = wide_entries / max(1, m.nnz)
+    kernel = "bellman_wide_kernel" if wide_share > 0.5 else "bellman_step_kernel"
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
     traffic = recorded_traffic(args.workload + ("" if args.dtype == "f64" else ":f32"))
     cfg = workload_config(args.workload, m, args.horizon)
@@ -344,8 +347,10 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "u64", "data": "synthetic (seeded banded IMDPs shaped like the paper's benchmark table)",
         "config": cfg,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_kind": peak_kind, "kernel": "bellman_step_kernel",
-                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": launch_ms},
+                     "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": launch_ms,
+                     "plan": {"tiles": n_tiles, "wide_states": n_wide, "wide_entry_share": wide_share},
+                     "timing": "CUDA events around each step's launches (both step kernels) / launches"},
         "clocks": clk,
         "gpu_launches": int(launches + args.steps),  # Bellman steps + one value-reset kernel per step
         "e2e": e2e,

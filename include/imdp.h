@@ -148,6 +148,13 @@ IMDP_API imdp_status imdp_model_info(const imdp_model* m, int32_t* n_states, int
  */
 IMDP_API imdp_status imdp_model_error_bound(const imdp_model* m, double* per_iteration);
 
+/* Launch plan of a model (no counterpart in the paper; host-only query): the
+ * number of tiles the tiled kernel streams, the number of wide states (a state
+ * whose entries exceed one tile or that has a column of 1280 entries or more,
+ * run by a whole CTA) and the entries of those wide states. Any output may be
+ * NULL. IMDP_EINVAL for a NULL model. */
+IMDP_API imdp_status imdp_model_plan(const imdp_model* m, int32_t* n_tiles, int32_t* n_wide, int64_t* wide_entries);
+
 /*
  * value_iteration / control_synthesis (Sec. 3.2) on one model.
  *   V_out         double[n_states] (host or device): V_k after the last iteration

@@ -147,6 +147,20 @@ imdp_status imdp_model_info(const imdp_model* m, int32_t* n_states, int32_t* n_c
   return IMDP_OK;
 }
 
+imdp_status imdp_model_plan(const imdp_model* m, int32_t* n_tiles, int32_t* n_wide, int64_t* wide_entries) {
+  set_error("");
+  if (!m || !m->dev) { set_error("NULL model"); return IMDP_EINVAL; }
+  const DevModel* d = m->dev;
+  if (n_tiles) *n_tiles = d->n_tiles;
+  if (n_wide) *n_wide = d->n_wide;
+  if (wide_entries) {
+    int64_t e = 0;
+    for (int32_t s : d->h_wide) e += d->h_colptr[d->h_stateptr[s + 1]] - d->h_colptr[d->h_stateptr[s]];
+    *wide_entries = e;
+  }
+  return IMDP_OK;
+}
+
 imdp_status imdp_model_error_bound(const imdp_model* m, double* per_iteration) {
   if (!m || !per_iteration) { set_error("NULL argument"); return IMDP_EINVAL; }
   *per_iteration = m->dev->err_bound;

@@ -972,6 +972,7 @@ __device__ bool wide_neighbor(const int32_t* __restrict__ rows, const Bounds<f32
   uint64_t best = 0, gs = 0, ds = 0, dk = 0;
   bool have = false;
   int32_t bi = -1;
+#pragma unroll 4
   for (int idx = tid; idx < k; idx += kWideThreads) {
     const uint64_t v = __ldg(V + rows[idx]);
     const uint64_t key = pess ? v : kOne - v;
@@ -1053,6 +1054,7 @@ __device__ uint64_t wide_search(const int32_t* __restrict__ rows, const Bounds<f
     return pess ? v : (kOne - v);
   };
   uint64_t cmin = ~0ull, cmax = 0;
+#pragma unroll 4
   for (int idx = tid; idx < k; idx += kWideThreads) {
     const uint64_t key = key_of(idx);
     cmin = key < cmin ? key : cmin;
@@ -1080,6 +1082,7 @@ __device__ uint64_t wide_search(const int32_t* __restrict__ rows, const Bounds<f
     }
     if (tid == 0) W.hsat[0] = W.hsat[1] = 0;
     __syncthreads();
+#pragma unroll 4
     for (int idx = tid; idx < k; idx += kWideThreads) {
       const uint64_t key = key_of(idx);
       if (key >= lo && key <= hi) {
@@ -1135,6 +1138,7 @@ __device__ uint64_t wide_search(const int32_t* __restrict__ rows, const Bounds<f
     hi = top < cmax ? top : cmax;
     if (cnt <= 32) break;
     uint64_t a = ~0ull, z = 0;
+#pragma unroll 4
     for (int idx = tid; idx < k; idx += kWideThreads) {
       const uint64_t key = key_of(idx);
       if (key >= lo && key <= hi) {
@@ -1153,6 +1157,7 @@ __device__ uint64_t wide_search(const int32_t* __restrict__ rows, const Bounds<f
   }
   __syncthreads();
   uint64_t acc = 0, gsum = 0, unused = 0;
+#pragma unroll 4
   for (int idx = tid; idx < k; idx += kWideThreads) {
     const uint64_t key = key_of(idx);
     const ulonglong2 b = lg[idx];
@@ -1227,7 +1232,8 @@ __device__ uint64_t wide_column_q(const int32_t* __restrict__ rows, const Bounds
   const int32_t entry = moving ? -2 - hint : hint;
   if (rem == 0) {
     uint64_t a = 0, f = 0, g = 0;
-    for (int idx = tid; idx < k; idx += kWideThreads) a += __umul64hi(__ldg(V + rows[idx]), lg[idx].x);
+#pragma unroll 4
+  for (int idx = tid; idx < k; idx += kWideThreads) a += __umul64hi(__ldg(V + rows[idx]), lg[idx].x);
     block_sum3(W, warp, lane, a, f, g);
     *hint_out = entry;
     return a;
@@ -1236,6 +1242,7 @@ __device__ uint64_t wide_column_q(const int32_t* __restrict__ rows, const Bounds
     const uint64_t vk = __ldg(V + rows[entry]);
     uint64_t acc = 0, flt = 0, geq = 0;
     uint32_t fc = 0, gc = 0;
+#pragma unroll 4
     for (int idx = tid; idx < k; idx += kWideThreads) {
       const uint64_t v = __ldg(V + rows[idx]);
       const ulonglong2 b = lg[idx];

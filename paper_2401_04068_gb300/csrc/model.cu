@@ -137,6 +137,22 @@ __global__ void quantize_columns_kernel(int32_t n_cols, const int32_t* __restric
   }
 }
 
+// Address at which kernels can read the array `p` in place, or nullptr if it
+// has to be copied to the device first.
+const double* device_view(const double* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+  if (a.type == cudaMemoryTypeHost) return (const double*)a.devicePointer;  // pinned, mapped
+  int dev = 0, pageable = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev);
+  return pageable ? p : nullptr;
+}
+
 // Staging buffer in stream order (cudaMallocAsync / cudaFreeAsync): creating a
 // model never waits for work that other streams have in flight (a plain
 // cudaFree would synchronize the whole device).
@@ -242,15 +258,18 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
   }
   m->bytes = sizeof(int32_t) * (ns_pad + nc_pad + nz_rows) + sizeof(ulonglong2) * nz + sizeof(uint64_t) * nr_pad;
 
-  // Bounds: device pointers are used in place, host arrays are staged.
+  // Bounds: the conversion kernel reads them in place when the device can
+  // (device memory, pinned host memory, and on systems where the GPU reads
+  // pageable host memory, such as Grace through NVLink-C2C, any host array);
+  // otherwise they are staged.
   DevBuf dlo, dup, derr;
-  const double* lo_d = lower;
-  const double* up_d = upper;
-  if (nnz > 0 && !is_device_pointer(lower)) {
+  const double* lo_d = nnz > 0 ? device_view(lower) : lower;
+  const double* up_d = nnz > 0 ? device_view(upper) : upper;
+  if (!lo_d) {
     if (!dlo.alloc(sizeof(double) * nz, st)) { model_destroy(m); set_error("staging allocation failed"); return IMDP_ENOMEM; }
     lo_d = (const double*)dlo.p;
   }
-  if (nnz > 0 && !is_device_pointer(upper)) {
+  if (!up_d) {
     if (!dup.alloc(sizeof(double) * nz, st)) { model_destroy(m); set_error("staging allocation failed"); return IMDP_ENOMEM; }
     up_d = (const double*)dup.p;
   }
@@ -263,8 +282,8 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
   if (e == cudaSuccess) e = cudaMemcpyAsync(m->colptr, hc.data(), sizeof(int32_t) * hc.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->rowval + nnz, 0, sizeof(int32_t) * (nz_rows - nnz), st);
   if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(m->rowval, rowval, sizeof(int32_t) * nnz, cudaMemcpyDefault, st);
-  if (e == cudaSuccess && lo_d != lower) e = cudaMemcpyAsync((void*)lo_d, lower, sizeof(double) * nnz, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && up_d != upper) e = cudaMemcpyAsync((void*)up_d, upper, sizeof(double) * nnz, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && dlo.p) e = cudaMemcpyAsync(dlo.p, lower, sizeof(double) * nnz, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && dup.p) e = cudaMemcpyAsync(dup.p, upper, sizeof(double) * nnz, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(derr.p, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) { model_destroy(m); return cuda_status(e, "upload model"); }
 

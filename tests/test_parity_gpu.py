@@ -103,7 +103,7 @@ def test_wide_and_tiled_states_mixed():
     for s in range(n):
         acts = 1 + (s % 3)
         for a in range(acts):
-            k = int(rng.integers(1100, 1300)) if (s % 7 == 0 and a == 0) else int(rng.integers(3, 60))
+            k = int(rng.integers(1290, 1390)) if (s % 7 == 0 and a == 0) else int(rng.integers(3, 60))
             dest = np.sort(rng.choice(n, size=k, replace=False))
             p = rng.random(k) + 0.01
             p /= p.sum()
@@ -117,6 +117,10 @@ def test_wide_and_tiled_states_mixed():
     m = IMDPInput(n, np.array(sp, np.int32), np.array(cp, np.int32), np.array(rv, np.int32), np.array(lo),
                   np.array(up), goal)
     model = _model(m)
+    n_tiles, n_wide, wide_entries = g.imdp_model_plan(model)
+    assert n_wide == 200 and n_tiles > 0
+    k = np.diff(m.colptr)
+    assert wide_entries == sum(int(k[m.stateptr[s]:m.stateptr[s + 1]].sum()) for s in range(0, n, 7))
     for pess, maxi in MODES:
         _compare(m, model, horizon=12, reach=m.goal, pessimistic=pess, maximize=maxi)
     small = random_imdp(30, max_actions=3, seed=78)

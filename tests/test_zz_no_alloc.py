@@ -63,3 +63,21 @@ def test_noalloc_infinite_horizon_and_limits():
     big = torch.zeros(n, dtype=torch.float64, device="cuda")
     with pytest.raises(g.ImdpError, match="131072"):
         g.imdp_value_iteration_noalloc(chain, g.make_spec(horizon=3, reach=[0]), big)
+
+
+def test_noalloc_with_wide_states_matches_regular():
+    # columns of ~1500-2500 entries: every state runs in the block-wide kernel,
+    # launched in the same stream (the entry point uses no second stream)
+    import torch
+    m = banded_imdp(2600, 1, 2600 * 2000 + 2600 + 1, eps=0.05, seed=33)
+    model = g.create_model(m)
+    for spec in [g.make_spec(horizon=30, reach=m.goal),
+                 g.make_spec(horizon=25, reach=m.goal, pessimistic=False, maximize=False)]:
+        ref = np.zeros(m.n_states)
+        g.imdp_value_iteration(model, spec, ref)
+        out = torch.zeros(m.n_states, dtype=torch.float64, device="cuda")
+        assert g.imdp_value_iteration_noalloc(model, spec, out) == g.IMDP_OK
+        # the entry point keeps no per-column threshold hints, so every column
+        # takes the full search, whose products are truncated in another grouping
+        # than the warm start's: equal up to K * k_max * 2^-62 (~2e-14 here)
+        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=1e-13)
