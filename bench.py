@@ -352,7 +352,8 @@ def run_ours(args, rank, world, local_rank):
                      "plan": {"tiles": n_tiles, "wide_states": n_wide, "wide_entry_share": wide_share},
                      "timing": "CUDA events around each step's launches (both step kernels) / launches"},
         "clocks": clk,
-        "gpu_launches": int(launches + args.steps),  # Bellman steps + one value-reset kernel per step
+        # step kernels (two per iteration when the model has wide states) + one value-reset kernel per step
+        "gpu_launches": int(launches * (2 if n_wide > 0 else 1) + args.steps),
         "e2e": e2e,
     }
     if world == 1 and not args.no_cpu_baseline:
