@@ -177,16 +177,43 @@ struct DevBuf {
 
 void model_destroy(DevModel* m) {
   if (!m) return;
-  cudaFree(m->stateptr);
-  cudaFree(m->colptr);
-  cudaFree(m->rowval);
-  cudaFree(m->lg);
-  cudaFree(m->rem);
-  cudaFree(m->tiles);
-  cudaFree(m->wide);
-  cudaFree(m->lg32);
-  cudaFree(m->shift);
+  // the model's buffers come from the stream-ordered pool; wait for all work
+  // that may still read them (what cudaFree would do) before handing them back
+  cudaDeviceSynchronize();
+  for (void* p : {(void*)m->stateptr, (void*)m->colptr, (void*)m->rowval, (void*)m->lg, (void*)m->rem,
+                  (void*)m->tiles, (void*)m->wide, (void*)m->lg32, (void*)m->shift})
+    if (p) cudaFreeAsync(p, nullptr);
+  cudaStreamSynchronize(nullptr);
   delete m;
+}
+
+// Device buffers of a model come from the device's default stream-ordered pool
+// (cudaMallocAsync on the creating stream): unlike cudaMalloc, this never waits
+// for kernels in flight (a server keeps creating models while it iterates), and
+// with the pool's release threshold raised, memory of destroyed models is
+// reused without being mapped again.
+template <class T>
+bool pool_alloc(T** p, size_t bytes, cudaStream_t st) {
+  static bool configured[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !configured[dev]) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    configured[dev] = true;
+  }
+  void* q = nullptr;
+  if (cudaMallocAsync(&q, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  *p = (T*)q;
+  return true;
 }
 
 imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, const int32_t* stateptr,
@@ -245,11 +272,10 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
   // 16-byte-aligned windows around any entry range stay inside the allocation.
   const size_t nz_rows = ((nz + 3) & ~size_t(3)) + 4;
   const size_t ns_pad = padded_i32(n_states + 1), nc_pad = padded_i32(n_cols + 1), nr_pad = padded_u64(n_cols);
-  const bool ok = cudaMalloc(&m->stateptr, sizeof(int32_t) * ns_pad) == cudaSuccess &&
-                  cudaMalloc(&m->colptr, sizeof(int32_t) * nc_pad) == cudaSuccess &&
-                  cudaMalloc(&m->rowval, sizeof(int32_t) * nz_rows) == cudaSuccess &&
-                  cudaMalloc(&m->lg, sizeof(ulonglong2) * nz) == cudaSuccess &&
-                  cudaMalloc(&m->rem, sizeof(uint64_t) * nr_pad) == cudaSuccess;
+  const bool ok = pool_alloc(&m->stateptr, sizeof(int32_t) * ns_pad, st) &&
+                  pool_alloc(&m->colptr, sizeof(int32_t) * nc_pad, st) &&
+                  pool_alloc(&m->rowval, sizeof(int32_t) * nz_rows, st) &&
+                  pool_alloc(&m->lg, sizeof(ulonglong2) * nz, st) && pool_alloc(&m->rem, sizeof(uint64_t) * nr_pad, st);
   if (!ok) {
     cudaGetLastError();
     model_destroy(m);
@@ -314,8 +340,7 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
     // re-encode the bounds in 32 bits and drop the 64-bit copy
     const size_t nz32 = ((nz + 1) & ~size_t(1)) + 2;  // padded for 16-byte bulk-copy windows
     DevBuf derr2;
-    if (cudaMalloc(&m->lg32, sizeof(uint2) * nz32) != cudaSuccess ||
-        cudaMalloc(&m->shift, sizeof(int32_t) * nc_pad) != cudaSuccess ||
+    if (!pool_alloc(&m->lg32, sizeof(uint2) * nz32, st) || !pool_alloc(&m->shift, sizeof(int32_t) * nc_pad, st) ||
         !derr2.alloc(sizeof(double) * n_cols, st)) {
       cudaGetLastError();
       model_destroy(m);
@@ -335,7 +360,7 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { model_destroy(m); return cuda_status(e, "32-bit storage"); }
     for (double x : herrs) m->err_bound = std::max(m->err_bound, x);
-    cudaFree(m->lg);
+    cudaFreeAsync(m->lg, st);
     m->lg = nullptr;
     m->bytes = m->bytes - sizeof(ulonglong2) * nz + sizeof(uint2) * nz32 + sizeof(int32_t) * nc_pad;
   }
@@ -346,8 +371,8 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
   m->n_wide = (int32_t)m->h_wide.size();
   std::vector<int2> wide2(m->h_wide.size());
   for (size_t i = 0; i < wide2.size(); ++i) wide2[i] = make_int2(0, m->h_wide[i]);
-  if (cudaMalloc(&m->tiles, sizeof(Tile) * std::max<size_t>(m->h_tiles.size(), 1)) != cudaSuccess ||
-      cudaMalloc(&m->wide, sizeof(int2) * std::max<size_t>(wide2.size(), 1)) != cudaSuccess) {
+  if (!pool_alloc(&m->tiles, sizeof(Tile) * std::max<size_t>(m->h_tiles.size(), 1), st) ||
+      !pool_alloc(&m->wide, sizeof(int2) * std::max<size_t>(wide2.size(), 1), st)) {
     cudaGetLastError();
     model_destroy(m);
     set_error("device allocation failed for the tile plan");
