@@ -1378,9 +1378,7 @@ void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out, std:
   }
 }
 
-int choose_col_class(int32_t) { return 1; }
-
-int bellman_grid(int, int) {
+int bellman_grid() {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -23,11 +23,6 @@ namespace imdp {
 
 constexpr uint64_t kOne = 1ull << 63;  // 1.0 in Q1.63
 
-// Column-size classes of the register-resident column routine: a warp keeps
-// up to 32 * E entries of one column in registers.
-constexpr int kWarpsPerBlock = 8;
-constexpr int kThreads = 32 * kWarpsPerBlock;
-
 // Property kinds inside the kernels.
 enum : int32_t { kPropReach = 0, kPropReachAvoid = 1, kPropReward = 2 };
 
@@ -146,7 +141,6 @@ struct StepLaunch {
   int32_t count;
   int32_t total_states;
   int32_t any_infinite;
-  int32_t col_class;  // unused by the tiled kernel (kept for the launch helpers)
   const Tile* tiles;
   int32_t n_tiles;
   int32_t n_wide;
@@ -160,8 +154,8 @@ struct StepLaunch {
 // when given) and the tiled kernel; the last CTA of the two advances the
 // iteration state.
 cudaError_t launch_bellman_step(const StepLaunch& L, int grid, cudaStream_t st, const SideStream* side = nullptr);
-int choose_col_class(int32_t max_col);
-int bellman_grid(int total_states, int col_class);
+// CTAs of the persistent tiled kernel: one per SM.
+int bellman_grid();
 // Tile plan for one problem's model (host): tiles appended to `out`, wide
 // states (no tile) appended to `wide`.
 void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out, std::vector<int32_t>& wide);

@@ -192,12 +192,11 @@ extern "C" IMDP_API imdp_status imdp_value_iteration_noalloc(imdp_model* m, cons
   L.count = 1;
   L.total_states = n;
   L.any_infinite = P.infinite;
-  L.col_class = choose_col_class(dm->max_col);
   L.tiles = dm->tiles;  // the model's own tile plan (problem index 0)
   L.n_tiles = dm->n_tiles;
   L.wide = dm->wide;
   L.n_wide = dm->n_wide;
-  const int grid = bellman_grid(n, L.col_class);
+  const int grid = bellman_grid();
   IterState hs;
   std::memset(&hs, 0, sizeof(hs));
   if (!P.infinite) {

@@ -387,12 +387,11 @@ struct Server {
       L.count = count;
       L.total_states = 0;
       L.any_infinite = 1;
-      L.col_class = 1;
       L.tiles = d_tiles;
       L.n_tiles = n_tiles;
       L.wide = d_wide;
       L.n_wide = n_wide;
-      const int grid = bellman_grid(0, 1);
+      const int grid = bellman_grid();
       cudaError_t e = cudaSuccess;
       for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = launch_bellman_step(L, grid, stream, &side);
       its.resize(count);

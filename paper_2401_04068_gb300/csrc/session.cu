@@ -145,7 +145,6 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   if (total >= (int64_t(1) << 31)) { delete S; set_error("batch too large"); return IMDP_EINVAL; }
   S->total = total;
   std::vector<uint8_t> fixed((size_t)total, 0);
-  int max_class = 1;
   for (int p = 0; p < count; ++p) {
     const imdp_spec* sp = specs[p];
     uint8_t* f = fixed.data() + S->base_h[p];
@@ -156,7 +155,6 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
         if (f[sp->avoid[i]] == 1) { delete S; set_error("a state is in both the reach and the avoid set"); return IMDP_EINVAL; }
         f[sp->avoid[i]] = 2;
       }
-    max_class = std::max(max_class, choose_col_class(ms[p]->max_col));
   }
   S->v_offset.assign(count, 0.0);
   S->v_scale.assign(count, 1.0);
@@ -268,7 +266,6 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   S->L.count = count;
   S->L.total_states = (int32_t)total;
   S->L.any_infinite = S->any_infinite ? 1 : 0;
-  S->L.col_class = max_class;
   S->L.tiles = S->tiles;
   S->L.n_tiles = S->n_tiles;
   S->L.wide = S->wide;
@@ -277,7 +274,7 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
     delete S;
     return cuda_status(e, "session side stream");
   }
-  S->grid = bellman_grid((int)total, max_class);
+  S->grid = bellman_grid();
   imdp_status r = S->reset(st);
   if (r != IMDP_OK) { delete S; return r; }
   *out = S;

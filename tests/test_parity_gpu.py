@@ -135,6 +135,48 @@ def test_wide_and_tiled_states_mixed():
         np.testing.assert_array_equal(out, alone)
 
 
+def _wide_model(seed, n=700, actions=2):
+    # every state has one column of >= 1280 entries (a wide state) next to short ones
+    rng = np.random.default_rng(seed)
+    sp, cp, rv, lo, up = [0], [0], [], [], []
+    for s in range(n):
+        for a in range(actions):
+            k = int(rng.integers(1290, 1400)) if a == 0 else int(rng.integers(5, 40))
+            k = min(k, n)
+            dest = np.sort(rng.choice(n, size=k, replace=False))
+            p = rng.random(k) + 0.01
+            p /= p.sum()
+            rv.extend(dest.tolist()), lo.extend((p * (1 - 0.1 * rng.random(k))).tolist())
+            up.extend(np.minimum(1.0, p * (1 + 0.1 * rng.random(k))).tolist())
+            cp.append(len(rv))
+        sp.append(len(cp) - 1)
+    from workloads import IMDPInput
+    return IMDPInput(n, np.array(sp, np.int32), np.array(cp, np.int32), np.array(rv, np.int32), np.array(lo),
+                     np.array(up), np.arange(300, 340, dtype=np.int32))
+
+
+def test_wide_states_rewards_infinite_horizon_and_policy():
+    m = _wide_model(79, n=1400)
+    model = _model(m)
+    n_tiles, n_wide, _ = g.imdp_model_plan(model)
+    assert n_wide == m.n_states and n_tiles == 0
+    r = np.linspace(-0.5, 1.5, m.n_states)
+    for pess, maxi in [(True, True), (False, False)]:
+        _compare(m, model, property=oracle.REWARD, horizon=20, reward=r, discount=0.9, pessimistic=pess,
+                 maximize=maxi)
+    _compare(m, model, property=oracle.REWARD, infinite_time=True, eps=1e-9, horizon=100000, reward=r,
+             discount=0.8)
+    _compare(m, model, infinite_time=True, eps=1e-9, horizon=100000, reach=m.goal, pessimistic=False)
+    avoid = np.arange(0, 30, dtype=np.int32)
+    _compare(m, model, property=oracle.REACH_AVOID, horizon=15, reach=m.goal, avoid=avoid)
+    # time-dependent policy rows from the block-wide argmax
+    K = 4
+    st, V, k, res, pol = g.value_iteration(model, m.n_states, policy=True, horizon=K, reach=m.goal)
+    for t in range(K):
+        _, Vp, _, _, _ = run_oracle(m, horizon=K - t - 1, reach=m.goal)
+        check_policy_row(m, Vp, pol[t], set(m.goal.tolist()), True, True)
+
+
 def test_reach_avoid():
     m = banded_imdp(400, 3, 400 * 3 * 13 + 1, eps=0.1, seed=8)
     model = _model(m)
