@@ -275,6 +275,26 @@ def test_dense_create_matches_csc(worked_example):
         np.testing.assert_array_equal(a, b)
 
 
+def test_dense_large_model_runs_wide():
+    # a dense model (every column lists all 1500 states, the layout of Sec. 3.1's
+    # dense matrices): every state is wide; against the oracle on the CSC form
+    rng = np.random.default_rng(91)
+    n, acts = 1500, 2
+    P = rng.random((n * acts, n)) ** 6 + 1e-6
+    P /= P.sum(axis=1, keepdims=True)
+    lo = P * (1 - 0.2 * rng.random(P.shape))
+    up = np.minimum(1.0, P * (1 + 0.2 * rng.random(P.shape)))
+    dm = g.imdp_create_dense(n, np.full(n, acts, np.int32), np.ascontiguousarray(lo.reshape(-1)),
+                             np.ascontiguousarray(up.reshape(-1)))
+    assert g.imdp_model_plan(dm)[1] == n
+    from workloads import IMDPInput
+    m = IMDPInput(n, (np.arange(n + 1) * acts).astype(np.int32), (np.arange(n * acts + 1) * n).astype(np.int32),
+                  np.tile(np.arange(n, dtype=np.int32), n * acts), lo.reshape(-1), up.reshape(-1),
+                  np.arange(700, 760, dtype=np.int32))
+    for pess, maxi in [(True, True), (False, True)]:
+        _compare(m, dm, horizon=12, reach=m.goal, pessimistic=pess, maximize=maxi)
+
+
 # --------------------------------------------------------------------------- errors
 
 def test_rejects_infeasible_and_malformed():
