@@ -113,9 +113,13 @@ IMDP_API const char* imdp_version(void);
  *   dtype          storage precision (IMDP_F64; IMDP_F32 halves the bound storage)
  *   stream         cudaStream_t used for the upload and checks
  *   out            receives the model handle (freed with imdp_model_destroy)
- * Inputs may be host or device pointers; they are copied. Returns IMDP_EINVAL for
- * broken structure, IMDP_EINFEASIBLE when a column is infeasible beyond an
- * absolute tolerance of 1e-12 on the sums.
+ * Inputs may be host or device pointers; the model keeps its own converted copy
+ * (the caller keeps ownership and may free them after the call). Bounds in device
+ * or pinned host memory, or in pageable host memory on systems where the GPU
+ * reads it (Grace), are converted in place without a staging copy. The call
+ * synchronizes `stream`. Returns IMDP_EINVAL for broken structure,
+ * IMDP_EINFEASIBLE when a column is infeasible beyond an absolute tolerance of
+ * 1e-12 on the sums, IMDP_ENOMEM when device memory runs out.
  */
 IMDP_API imdp_status imdp_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, const int32_t* stateptr,
                             const int32_t* colptr, const int32_t* rowval, const double* lower,
@@ -132,7 +136,8 @@ IMDP_API imdp_status imdp_create_csc(int32_t n_states, int32_t n_cols, int64_t n
 IMDP_API imdp_status imdp_create_dense(int32_t n_states, const int32_t* n_actions, const double* lower,
                               const double* upper, imdp_dtype dtype, void* stream, imdp_model** out);
 
-/* Free a model and its device memory. NULL is ignored. */
+/* Free a model and its device memory (waits for the device first, as work in
+ * flight may still read it). NULL is ignored. */
 IMDP_API void imdp_model_destroy(imdp_model* m);
 
 /* Model dimensions and the device bytes it holds. Any output may be NULL. */
