@@ -48,7 +48,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstddef>
+#include <mutex>
 
 #include "imdp_internal.h"
 
@@ -1386,21 +1388,27 @@ int bellman_grid() {
 }
 
 cudaError_t launch_bellman_step(const StepLaunch& L0, int grid, cudaStream_t st, const SideStream* side) {
-  static int configured[64] = {0};
+  // per-device setup, once (sessions, servers and the allocation-free entry
+  // point may launch from several threads)
+  static std::atomic<int> configured[64];
   static int wide_blocks[64] = {0};
+  static std::mutex setup;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (!configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(bellman_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(Smem));
-    if (e != cudaSuccess) return e;
-    int per_sm = 1, sms = 152;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_wide_kernel, kWideThreads, 0);
-    if (e != cudaSuccess) return e;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    wide_blocks[dev] = std::max(1, per_sm) * sms;
-    configured[dev] = 1;
+  if (!configured[dev].load(std::memory_order_acquire)) {
+    std::lock_guard<std::mutex> lk(setup);
+    if (!configured[dev].load(std::memory_order_relaxed)) {
+      cudaError_t e = cudaFuncSetAttribute(bellman_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sizeof(Smem));
+      if (e != cudaSuccess) return e;
+      int per_sm = 1, sms = 152;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_wide_kernel, kWideThreads, 0);
+      if (e != cudaSuccess) return e;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      wide_blocks[dev] = std::max(1, per_sm) * sms;
+      configured[dev].store(1, std::memory_order_release);
+    }
   }
   StepLaunch L = L0;
   const int mg = L.n_tiles > 0 ? grid : 1;  // one CTA still takes part in the end-of-launch ticket

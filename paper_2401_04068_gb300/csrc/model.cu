@@ -9,6 +9,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "imdp_internal.h"
 
 namespace imdp {
@@ -194,17 +196,16 @@ void model_destroy(DevModel* m) {
 // reused without being mapped again.
 template <class T>
 bool pool_alloc(T** p, size_t bytes, cudaStream_t st) {
-  static bool configured[64] = {false};
+  static std::atomic<bool> configured[64];
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !configured[dev]) {
+  if (dev >= 0 && dev < 64 && !configured[dev].exchange(true)) {  // once per device (idempotent)
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
       uint64_t keep = ~0ull;
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     cudaGetLastError();
-    configured[dev] = true;
   }
   void* q = nullptr;
   if (cudaMallocAsync(&q, bytes, st) != cudaSuccess) {
