@@ -1,0 +1,41 @@
+"""Bookkeeping of bench.py on the CPU: algorithmic bytes, the traffic record's
+source-hash check, and the whole-job timing reduction at one rank."""
+import json
+import os
+
+import numpy as np
+
+import bench
+from workloads import banded_imdp
+
+
+def test_algorithmic_bytes_formula():
+    m = banded_imdp(100, 2, 100 * 2 * 10 + 1, seed=3)
+    assert bench.algorithmic_bytes_per_iteration(m) == 20 * m.nnz + 12 * m.n_cols + 20 * m.n_states
+    assert bench.algorithmic_bytes_per_iteration(m, "f32") == 12 * m.nnz + 16 * m.n_cols + 20 * m.n_states
+
+
+def test_traffic_record_only_for_the_kernel_it_was_taken_on(tmp_path, monkeypatch):
+    root = tmp_path
+    (root / "profiles").mkdir()
+    (root / "paper_2401_04068_gb300" / "csrc").mkdir(parents=True)
+    for f in ("bellman.cu", "imdp_internal.h"):
+        (root / "paper_2401_04068_gb300" / "csrc" / f).write_text("kernel " + f)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    h = bench.bellman_source_hash()
+    rec = {"w": {"source_hash": h, "dram_bytes_per_launch": 123}, "old": {"source_hash": "0" * 16,
+                                                                          "dram_bytes_per_launch": 9}}
+    (root / "profiles" / "bellman_step_traffic.json").write_text(json.dumps(rec))
+    assert bench.recorded_traffic("w") == 123
+    assert bench.recorded_traffic("old") is None  # taken on another kernel source
+    assert bench.recorded_traffic("missing") is None
+    (root / "paper_2401_04068_gb300" / "csrc" / "bellman.cu").write_text("changed")
+    assert bench.recorded_traffic("w") is None
+
+
+def test_committed_traffic_record_is_well_formed():
+    p = os.path.join(bench.ROOT, "profiles", "bellman_step_traffic.json")
+    rec = json.load(open(p))
+    for name, r in rec.items():
+        assert len(r["source_hash"]) == 16 and r["dram_bytes_per_launch"] > 0
+    assert np.isfinite(bench.measured_peak_hbm()[0])
