@@ -160,6 +160,14 @@ IMDP_API imdp_status imdp_model_error_bound(const imdp_model* m, double* per_ite
  * NULL. IMDP_EINVAL for a NULL model. */
 IMDP_API imdp_status imdp_model_plan(const imdp_model* m, int32_t* n_tiles, int32_t* n_wide, int64_t* wide_entries);
 
+/* Test hook for failure detection (no counterpart in the paper). While `on` is
+ * nonzero, step launches of the tiled kernel issue no tile copies: every
+ * consumer wait runs into its bound (about 2 s), the kernel records the error
+ * and returns, and the next read of the session reports IMDP_ETIMEOUT; the
+ * CUDA context stays usable (reset the session and run again). Process-wide;
+ * not for production use. */
+IMDP_API void imdp_debug_stall_producer(int32_t on);
+
 /*
  * value_iteration / control_synthesis (Sec. 3.2) on one model.
  *   V_out         double[n_states] (host or device): V_k after the last iteration

@@ -30,7 +30,7 @@ EXPORTED = [
     "imdp_session_launches", "imdp_session_destroy", "imdp_value_iteration_noalloc",
     "imdp_server_create", "imdp_server_submit", "imdp_server_poll", "imdp_server_wait", "imdp_server_destroy",
     "imdp_model_error_bound", "imdp_partition_states", "imdp_create_csc_slice", "imdp_session_values_get",
-    "imdp_session_values_put", "imdp_model_plan",
+    "imdp_session_values_put", "imdp_model_plan", "imdp_debug_stall_producer",
 ]
 
 
@@ -112,6 +112,8 @@ def load(path: Optional[str] = None):
     lib.imdp_model_error_bound.restype = C.c_int
     lib.imdp_server_destroy.argtypes = [vp]
     lib.imdp_server_destroy.restype = None
+    lib.imdp_debug_stall_producer.argtypes = [C.c_int32]
+    lib.imdp_debug_stall_producer.restype = None
     lib.imdp_model_plan.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
     lib.imdp_model_plan.restype = C.c_int
     lib.imdp_partition_states.argtypes = [C.c_int32, vp, vp, C.c_int32, vp]
@@ -492,3 +494,8 @@ def imdp_model_plan(model: Model):
     t, w, e = C.c_int32(0), C.c_int32(0), C.c_int64(0)
     _check(load().imdp_model_plan(C.c_void_p(model.handle), C.byref(t), C.byref(w), C.byref(e)), "imdp_model_plan")
     return t.value, w.value, e.value
+
+
+def imdp_debug_stall_producer(on: bool):
+    """Test hook: step launches leave every consumer wait unsatisfied (see include/imdp.h)."""
+    load().imdp_debug_stall_producer(1 if on else 0)

@@ -147,6 +147,8 @@ imdp_status imdp_model_info(const imdp_model* m, int32_t* n_states, int32_t* n_c
   return IMDP_OK;
 }
 
+void imdp_debug_stall_producer(int32_t on) { g_stall_producer.store(on ? 1 : 0); }
+
 imdp_status imdp_model_plan(const imdp_model* m, int32_t* n_tiles, int32_t* n_wide, int64_t* wide_entries) {
   set_error("");
   if (!m || !m->dev) { set_error("NULL model"); return IMDP_EINVAL; }

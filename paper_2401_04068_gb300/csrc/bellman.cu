@@ -713,7 +713,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
 
   if (warp == kConsumerWarps) {
     // ------------------------------------------------------------ producer
-    if (lane == 0) {
+    if (lane == 0 && !L.stall) {
       int i = 0;
       bool ok = true;
       int pending_round[kStages];
@@ -1281,7 +1281,7 @@ __device__ uint64_t wide_column_q(const int32_t* __restrict__ rows, const Bounds
 // room one persistent tiled CTA leaves on each SM) or before it: both read
 // V_{k-1} and write disjoint states of V_k, and whichever CTA of the two
 // kernels finishes last advances the iteration state.
-__global__ void __launch_bounds__(kWideThreads, 512 / kWideThreads) bellman_wide_kernel(StepLaunch L) {
+__global__ void __launch_bounds__(kWideThreads, 6) bellman_wide_kernel(StepLaunch L) {
   __shared__ WideShared W;
   __shared__ int take;
   __shared__ int is_last;
@@ -1387,6 +1387,8 @@ int bellman_grid() {
   return sms;  // persistent: one CTA per SM
 }
 
+std::atomic<int> g_stall_producer{0};
+
 cudaError_t launch_bellman_step(const StepLaunch& L0, int grid, cudaStream_t st, const SideStream* side) {
   // per-device setup, once (sessions, servers and the allocation-free entry
   // point may launch from several threads)
@@ -1411,6 +1413,7 @@ cudaError_t launch_bellman_step(const StepLaunch& L0, int grid, cudaStream_t st,
     }
   }
   StepLaunch L = L0;
+  L.stall = g_stall_producer.load(std::memory_order_relaxed);
   const int mg = L.n_tiles > 0 ? grid : 1;  // one CTA still takes part in the end-of-launch ticket
   const int wg = L.n_wide > 0 ? std::min(L.n_wide, wide_blocks[dev]) : 0;
   L.grid_total = mg + wg;

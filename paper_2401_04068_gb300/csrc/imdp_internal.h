@@ -13,9 +13,11 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <atomic>
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/imdp.h"
 
@@ -146,10 +148,20 @@ struct StepLaunch {
   int32_t n_wide;
   const int2* wide;  // (problem, state) of every wide state
   int32_t grid_total;  // CTAs of both step kernels in this launch (set by the launcher)
-  int32_t _pad3;
+  int32_t stall;       // test hook: the producer issues nothing, so every wait runs out
+};
+
+// NVTX range for the host-side phases (model upload, session steps, server
+// chunks); shows up in Nsight timelines, free when no tool is attached.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
 };
 
 // bellman.cu
+// Test hook (imdp_debug_stall_producer): launches made while set leave the
+// consumers' waits unsatisfied, to exercise the bounded-wait error path.
+extern std::atomic<int> g_stall_producer;
 // One Bellman iteration: the wide-state kernel (on `side`, beside the tiled one,
 // when given) and the tiled kernel; the last CTA of the two advances the
 // iteration state.

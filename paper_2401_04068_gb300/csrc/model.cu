@@ -221,6 +221,7 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
                              const int32_t* colptr, const int32_t* rowval, const double* lower,
                              const double* upper, imdp_dtype dtype, cudaStream_t st, DevModel** out,
                              int32_t own0, int32_t own1) {
+  TraceRange trace("imdp model create");
   if (!out) { set_error("out is NULL"); return IMDP_EINVAL; }
   *out = nullptr;
   if (own1 < 0) own1 = n_states;

@@ -392,6 +392,7 @@ struct Server {
       L.wide = d_wide;
       L.n_wide = n_wide;
       const int grid = bellman_grid();
+      TraceRange trace("imdp server chunk");
       cudaError_t e = cudaSuccess;
       for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = launch_bellman_step(L, grid, stream, &side);
       its.resize(count);

@@ -282,6 +282,7 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
 }
 
 imdp_status Session::reset(cudaStream_t st) {
+  TraceRange trace("imdp session reset");
   init_values_kernel<<<(int)std::min<int64_t>((total + 255) / 256, 8192), 256, 0, st>>>(total, fixed, V);
   cudaError_t e = cudaGetLastError();
   for (int p = 0; p < count && e == cudaSuccess; ++p)
@@ -303,6 +304,7 @@ imdp_status Session::reset(cudaStream_t st) {
 
 imdp_status Session::step(int32_t n, cudaStream_t st) {
   if (n <= 0) return IMDP_OK;
+  TraceRange trace("imdp session step");
   cudaError_t e = cudaSuccess;
   int32_t done = 0;
   if (st != nullptr && n >= kGraphChunk) {
