@@ -369,7 +369,9 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": launch_ms,
-                     "plan": {"tiles": n_tiles, "wide_states": n_wide, "wide_entry_share": wide_share},
+                     "plan": {"tiles": n_tiles, "wide_states": n_wide, "wide_entry_share": wide_share,
+                              # the launcher's rule: 24-warp CTAs for >= 16 columns per tile, no wide states
+                              "tiled_cta_warps": 24 if (n_wide == 0 and len(m.colptr) - 1 >= 16 * n_tiles) else 16},
                      "timing": "CUDA events around each step's launches (both step kernels) / launches"},
         "clocks": clk,
         # step kernels (two per iteration when the model has wide states) + one value-reset kernel per step

@@ -6,13 +6,15 @@
 // Data movement. The launch is persistent (one CTA per SM). The model is cut into
 // state-aligned tiles (consecutive states of one problem, <= kTileEntries
 // entries); states that do not fit a stage or that have columns of kWideCol
-// entries or more are "wide" and run in bellman_wide_kernel (a whole CTA per
-// state, launched just before). A producer warp streams each tile's destination indices and bound
-// pairs into a three-stage shared-memory ring with bulk asynchronous copies
-// (cp.async.bulk, completion counted on an mbarrier), while fifteen consumer
-// warps work on the tiles already landed (16 warps: four per SM sub-partition,
-// which leaves 128 registers per thread). Every entry crosses HBM once per
-// iteration.
+// entries or more are "wide" and run in bellman_wide_kernel (a 4-warp CTA per
+// state, beside this kernel on a second stream, or before it). A producer warp
+// streams each tile's destination indices and bound pairs into a three-stage
+// shared-memory ring with bulk asynchronous copies
+// (cp.async.bulk, completion counted on an mbarrier), while the consumer warps
+// work on the tiles already landed: 15 of them (16 warps, four per SM
+// sub-partition, 96 registers per thread), or 23 (24 warps, 80 registers) when
+// the tiles hold 16 or more columns on average, where the extra warps hide more
+// of the V gathers' latency. Every entry crosses HBM once per iteration.
 //
 // O-maximization without a sort. For a pessimistic adversary the procedure of
 // Sec. 4 orders the destinations by ascending V, starts from p = lower and hands
@@ -60,9 +62,13 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBins = 64;
-constexpr int kConsumerWarps = 15;
+// Consumer warps per CTA of the tiled kernel (plus one producer warp): 15 (96
+// registers per thread) in general, 23 (80 registers) for tiles of many short
+// columns, where more warps in flight hide more of the gathers' latency.
+constexpr int kConsumersLong = 15;
+constexpr int kConsumersShort = 23;
+constexpr int kShortColsPerTile = 16;  // mean columns per tile that selects 23
 constexpr int kStages = 3;
-constexpr int kBlockThreads = 32 * (kConsumerWarps + 1);
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz: bound of every wait
 
 // Per-warp scratch. The histogram is dead by the time the candidate list is
@@ -103,9 +109,10 @@ struct Stage {
   unsigned int done;                     // slots of this tile finished so far
 };
 
+template <int W>
 struct Smem {
   Stage st[kStages];
-  WarpScratch ws[kConsumerWarps];
+  WarpScratch ws[W];
   unsigned long long full[kStages];
   unsigned long long empty[kStages];
   int is_last;
@@ -115,7 +122,8 @@ static_assert(offsetof(Stage, rem) % 16 == 0 && offsetof(Stage, sptr) % 16 == 0 
                   offsetof(Stage, fixed) % 16 == 0 && offsetof(Stage, prob) % 16 == 0 && offsetof(Stage, hint) % 16 == 0 && offsetof(Stage, shift) % 16 == 0 && sizeof(Problem) % 16 == 0,
               "bulk-copy destinations must be 16-byte aligned");
 static_assert(sizeof(Stage) % 16 == 0, "stage alignment");
-static_assert(sizeof(Smem) <= 232448, "shared memory budget of one CTA");
+static_assert(sizeof(Smem<kConsumersLong>) <= 232448 && sizeof(Smem<kConsumersShort>) <= 232448,
+              "shared memory budget of one CTA");
 
 // ---------------------------------------------------------------- PTX helpers
 
@@ -694,9 +702,10 @@ __device__ __forceinline__ void stage_column(Stage& st, const Tile& T, int32_t l
 
 __device__ void end_of_launch(const StepLaunch& L, int* is_last);
 
-__global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaunch L) {
+template <int W>
+__global__ void __launch_bounds__(32 * (W + 1), 1) bellman_step_kernel(StepLaunch L) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  Smem<W>& S = *reinterpret_cast<Smem<W>*>(smem_raw);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   unsigned* err = &L.ctl->error;
@@ -705,13 +714,13 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
     for (int s = 0; s < kStages; ++s) {
       S.st[s].done = 0;  // shared memory starts undefined in every launch
       mbar_init(&S.full[s], 1);
-      mbar_init(&S.empty[s], kConsumerWarps);
+      mbar_init(&S.empty[s], W);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  if (warp == kConsumerWarps) {
+  if (warp == W) {
     // ------------------------------------------------------------ producer
     if (lane == 0 && !L.stall) {
       int i = 0;
@@ -804,10 +813,10 @@ __global__ void __launch_bounds__(kBlockThreads, 1) bellman_step_kernel(StepLaun
       const int32_t nslots = T.c1 - T.c0;
       const int32_t k_iter = st.k_iter;
       const bool active = st.active != 0;
-      // first local slot of this warp: global slot g with g % kConsumerWarps == warp
-      int32_t first = warp - (slot_base % kConsumerWarps);
-      if (first < 0) first += kConsumerWarps;
-      for (int32_t ls = first; ls < nslots; ls += kConsumerWarps) {
+      // first local slot of this warp: global slot g with g % W == warp
+      int32_t first = warp - (slot_base % W);
+      if (first < 0) first += W;
+      for (int32_t ls = first; ls < nslots; ls += W) {
         if (active) {
           if (st.prob.lg32)
             stage_column<true>(st, T, ls, k_iter, ws, lane);
@@ -1401,8 +1410,12 @@ cudaError_t launch_bellman_step(const StepLaunch& L0, int grid, cudaStream_t st,
   if (!configured[dev].load(std::memory_order_acquire)) {
     std::lock_guard<std::mutex> lk(setup);
     if (!configured[dev].load(std::memory_order_relaxed)) {
-      cudaError_t e = cudaFuncSetAttribute(bellman_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)sizeof(Smem));
+      cudaError_t e = cudaFuncSetAttribute(bellman_step_kernel<kConsumersLong>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sizeof(Smem<kConsumersLong>));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(bellman_step_kernel<kConsumersShort>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(Smem<kConsumersShort>));
       if (e != cudaSuccess) return e;
       int per_sm = 1, sms = 152;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_wide_kernel, kWideThreads, 0);
@@ -1417,6 +1430,17 @@ cudaError_t launch_bellman_step(const StepLaunch& L0, int grid, cudaStream_t st,
   const int mg = L.n_tiles > 0 ? grid : 1;  // one CTA still takes part in the end-of-launch ticket
   const int wg = L.n_wide > 0 ? std::min(L.n_wide, wide_blocks[dev]) : 0;
   L.grid_total = mg + wg;
+  // 23 consumer warps for tiles of many short columns; never beside wide CTAs
+  // (a 24-warp CTA leaves no registers for one)
+  const bool short_cols = wg == 0 && L.tile_cols >= (int64_t)kShortColsPerTile * L.n_tiles;
+  const auto tiled = [&](cudaStream_t s) {
+    if (short_cols)
+      bellman_step_kernel<kConsumersShort>
+          <<<mg, 32 * (kConsumersShort + 1), sizeof(Smem<kConsumersShort>), s>>>(L);
+    else
+      bellman_step_kernel<kConsumersLong><<<mg, 32 * (kConsumersLong + 1), sizeof(Smem<kConsumersLong>), s>>>(L);
+    return cudaGetLastError();
+  };
   cudaError_t e = cudaSuccess;
   if (wg > 0 && side && side->stream && L.n_tiles > 0) {
     // fork / join: the tiled kernel is issued first so that its persistent CTAs
@@ -1424,8 +1448,7 @@ cudaError_t launch_bellman_step(const StepLaunch& L0, int grid, cudaStream_t st,
     e = cudaEventRecord(side->fork, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(side->stream, side->fork, 0);
     if (e != cudaSuccess) return e;
-    bellman_step_kernel<<<mg, kBlockThreads, sizeof(Smem), st>>>(L);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = tiled(st)) != cudaSuccess) return e;
     bellman_wide_kernel<<<wg, kWideThreads, 0, side->stream>>>(L);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = cudaEventRecord(side->join, side->stream);
@@ -1436,8 +1459,7 @@ cudaError_t launch_bellman_step(const StepLaunch& L0, int grid, cudaStream_t st,
     bellman_wide_kernel<<<wg, kWideThreads, 0, st>>>(L);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  bellman_step_kernel<<<mg, kBlockThreads, sizeof(Smem), st>>>(L);
-  return cudaGetLastError();
+  return tiled(st);
 }
 
 }  // namespace imdp

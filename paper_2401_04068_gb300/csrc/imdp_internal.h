@@ -68,6 +68,7 @@ struct DevModel {
   std::vector<Tile> h_tiles;        // tile plan of this model (problem index 0)
   Tile* tiles = nullptr;            // device copy of h_tiles
   int32_t n_tiles = 0;
+  int64_t tile_cols = 0;            // columns in all of h_tiles
   std::vector<int32_t> h_wide;      // wide states (in no tile)
   int2* wide = nullptr;             // device copy as (problem 0, state)
   int32_t n_wide = 0;
@@ -147,6 +148,7 @@ struct StepLaunch {
   int32_t n_tiles;
   int32_t n_wide;
   const int2* wide;  // (problem, state) of every wide state
+  int64_t tile_cols;   // columns in all tiles (the launcher picks the CTA shape from it)
   int32_t grid_total;  // CTAs of both step kernels in this launch (set by the launcher)
   int32_t stall;       // test hook: the producer issues nothing, so every wait runs out
 };

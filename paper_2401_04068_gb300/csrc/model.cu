@@ -370,6 +370,7 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
   m->h_colptr = std::move(hc);
   plan_tiles(m, 0, m->h_tiles, m->h_wide);
   m->n_tiles = (int32_t)m->h_tiles.size();
+  for (const Tile& t : m->h_tiles) m->tile_cols += t.c1 - t.c0;
   m->n_wide = (int32_t)m->h_wide.size();
   std::vector<int2> wide2(m->h_wide.size());
   for (size_t i = 0; i < wide2.size(); ++i) wide2[i] = make_int2(0, m->h_wide[i]);

@@ -194,6 +194,7 @@ extern "C" IMDP_API imdp_status imdp_value_iteration_noalloc(imdp_model* m, cons
   L.any_infinite = P.infinite;
   L.tiles = dm->tiles;  // the model's own tile plan (problem index 0)
   L.n_tiles = dm->n_tiles;
+  L.tile_cols = dm->tile_cols;
   L.wide = dm->wide;
   L.n_wide = dm->n_wide;
   const int grid = bellman_grid();

@@ -254,6 +254,7 @@ struct Server {
   imdp_status upload_tables(int32_t count) {
     std::vector<Tile> tiles;
     std::vector<int2> wide;
+    int64_t cols = 0;
     for (int32_t s = 0; s < count; ++s) {
       Request* r = slots[s];
       if (!r) continue;
@@ -261,6 +262,7 @@ struct Server {
       tiles.insert(tiles.end(), r->model->h_tiles.begin(), r->model->h_tiles.end());
       for (size_t t = at; t < tiles.size(); ++t) tiles[t].p = s;
       for (int32_t st : r->model->h_wide) wide.push_back(make_int2(s, st));
+      cols += r->model->tile_cols;
     }
     if (wide.size() > wide_cap) {
       cudaFree(d_wide);
@@ -295,10 +297,12 @@ struct Server {
     if (e != cudaSuccess) return cuda_status(e, "server tables");
     n_tiles = (int32_t)tiles.size();
     n_wide = (int32_t)wide.size();
+    tile_cols = cols;
     return IMDP_OK;
   }
 
   int32_t n_tiles = 0;
+  int64_t tile_cols = 0;
   int32_t n_wide = 0;
   SideStream side;
   int2* d_wide = nullptr;
@@ -389,6 +393,7 @@ struct Server {
       L.any_infinite = 1;
       L.tiles = d_tiles;
       L.n_tiles = n_tiles;
+      L.tile_cols = tile_cols;
       L.wide = d_wide;
       L.n_wide = n_wide;
       const int grid = bellman_grid();

@@ -268,6 +268,8 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   S->L.any_infinite = S->any_infinite ? 1 : 0;
   S->L.tiles = S->tiles;
   S->L.n_tiles = S->n_tiles;
+  S->L.tile_cols = 0;
+  for (int p = 0; p < count; ++p) S->L.tile_cols += ms[p]->tile_cols;
   S->L.wide = S->wide;
   S->L.n_wide = S->n_wide;
   if (S->n_wide > 0 && S->n_tiles > 0 && (e = S->side.create()) != cudaSuccess) {

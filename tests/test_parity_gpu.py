@@ -241,6 +241,29 @@ def test_batch_equals_alone_bitwise():
     np.testing.assert_array_equal(dev.cpu().numpy(), outs[0])
 
 
+def test_cta_shapes_agree_to_the_bit():
+    # tiles of many short columns run in 24-warp CTAs, others (and every launch
+    # with wide states) in 16-warp CTAs; a column's words do not depend on which
+    m = banded_imdp(3000, 1, 3000 * 24 + 1, seed=91)
+    model = _model(m)
+    n_tiles, n_wide, _ = g.imdp_model_plan(model)
+    assert n_wide == 0 and len(m.colptr) - 1 >= 16 * n_tiles  # the 24-warp shape alone
+    spec = g.make_spec(horizon=25, reach=m.goal)
+    alone = np.zeros(m.n_states)
+    g.imdp_value_iteration(model, spec, alone)
+    _, oV, _, _, _ = run_oracle(m, horizon=25, reach=m.goal)
+    np.testing.assert_allclose(alone, oV, rtol=0, atol=TOL_F64)
+    w = _wide_model(92, n=1300, actions=1)
+    wm = _model(w)
+    assert g.imdp_model_plan(wm)[1] > 0  # a batch with wide states: the 16-warp shape
+    outs = [np.zeros(m.n_states), np.zeros(w.n_states)]
+    g.imdp_value_iteration_batch([model, wm], [spec, g.make_spec(horizon=25, reach=w.goal)], outs, [0, 0])
+    np.testing.assert_array_equal(outs[0], alone)
+    wa = np.zeros(w.n_states)
+    g.imdp_value_iteration(wm, g.make_spec(horizon=25, reach=w.goal), wa)
+    np.testing.assert_array_equal(outs[1], wa)
+
+
 def test_device_inputs():
     import torch
     m = banded_imdp(200, 2, 200 * 2 * 12 + 1, seed=12)
