@@ -317,12 +317,16 @@ __device__ __forceinline__ bool column_warm(const int32_t* rows, const Bounds<f3
   if (hint < 0 || hint >= k) return false;
   const uint64_t vk = __ldg(V + rows[hint]);
   uint64_t acc = 0, flt = 0, geq = 0;
-  if (narrow_of(rem_word))
+  if (narrow_of(rem_word)) {
+    // every gap sum of a narrow column is below 2^64: plain exact sums
     warm_pass<false>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
-  else
+    flt = warp_sum_u64(flt);
+    geq = warp_sum_u64(geq);
+  } else {
     warm_pass<true>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
-  flt = warp_sum_sat(flt);
-  geq = warp_sum_sat(geq);
+    flt = warp_sum_sat(flt);
+    geq = warp_sum_sat(geq);
+  }
   acc = warp_sum_u64(acc);
   if (flt < rem && rem - flt <= geq) {
     *q = acc + __umul64hi(vk, rem - flt);
