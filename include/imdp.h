@@ -58,7 +58,8 @@ typedef enum {
   IMDP_EBUSY = 6,        /* the server has no free slot; retry later */
   IMDP_ENOCONV = 7,      /* infinite horizon: residual still >= eps at the iteration cap */
   IMDP_ENOTFOUND = 8,    /* unknown server ticket */
-  IMDP_EPENDING = 9      /* server ticket not finished yet */
+  IMDP_EPENDING = 9,     /* server ticket not finished yet */
+  IMDP_EIO = 10          /* a model file cannot be opened, read or written */
 } imdp_status;
 
 /* Storage precision of the transition bounds. IMDP_F64 keeps 64 bits per bound
@@ -318,6 +319,85 @@ IMDP_API imdp_status imdp_server_poll(imdp_server* s, uint64_t ticket, double* V
 IMDP_API imdp_status imdp_server_wait(imdp_server* s, uint64_t ticket, double timeout_ms, double* V_out,
                                       int32_t* k_out, double* latency_ms);
 IMDP_API void imdp_server_destroy(imdp_server* s);
+
+/*
+ * Model files (Sec. 3.1, reading and writing IMDPs): the PRISM explicit format
+ * (four files sharing one path stem: .sta states, .lab labels, .tra interval
+ * transitions, .pctl the property) and the bmdp-tool format (one file: source,
+ * action, destination and the two bounds per line, plus the terminal states).
+ * These calls run on the host only and need no CUDA device.
+ *
+ * bmdp-tool layout (whitespace-separated ASCII, 0-based indices):
+ *     n_states
+ *     n_actions                (the largest number of actions of a state)
+ *     n_terminal
+ *     t_1 ... t_n_terminal     (terminal states)
+ *     s a s' lower upper       (one line per stored transition, any order)
+ * The format stores no horizon and no modes: a read sets spec.property =
+ * IMDP_REACH, spec.reach = the terminal states, horizon 0, finite time,
+ * pessimistic, maximize, and the caller sets what the query needs.
+ *
+ * PRISM explicit layout (0-based indices):
+ *     .sta  "(vars)" then one line "i:(values)" per state i
+ *     .lab  0="init" 1="deadlock" ... (label ids and names) on the first line,
+ *           then "s: id id ..." per labelled state
+ *     .tra  "n_states n_choices n_transitions" then "s c s' [lower,upper]" per
+ *           transition (a plain probability p reads as [p,p]; a trailing action
+ *           name is ignored); the choices of a state are numbered 0, 1, ...
+ *     .pctl one property: P<strategy><adversary>=? [ F "goal" ], [ F<=K "goal" ],
+ *           [ !"avoid" U "goal" ] or [ !"avoid" U<=K "goal" ], with strategy and
+ *           adversary each max or min (adversary min = pessimistic); a missing
+ *           adversary (Pmax=?, Pmin=?) reads as pessimistic. Without a bound the
+ *           property is infinite-time with eps = 1e-6. Reward properties have no
+ *           place in these four files and are rejected.
+ *
+ * A state that has no transition in the file is read as absorbing: one column
+ * holding the self-loop [1, 1], whose `action` entry is -1. Columns of a state
+ * are ordered by the file's action (choice) index, destinations ascending.
+ * Reads check the structure (indices in range, no duplicate transition, counts
+ * that match the headers, finite bounds) and return IMDP_EINVAL with
+ * "file:line: reason" in imdp_last_error(); feasibility of the intervals is
+ * checked when the arrays are passed to imdp_create_csc. A file that cannot be
+ * opened or written returns IMDP_EIO. Writers print bounds with 17 significant
+ * digits, so a write followed by a read returns the same binary64 values.
+ */
+typedef struct {
+  int32_t n_states;
+  int32_t n_cols;
+  int64_t nnz;
+  int32_t* stateptr; /* int32[n_states + 1] */
+  int32_t* colptr;   /* int32[n_cols + 1] */
+  int32_t* rowval;   /* int32[nnz], strictly increasing within a column */
+  double* lower;     /* double[nnz] */
+  double* upper;     /* double[nnz] */
+  int32_t* action;   /* int32[n_cols]: the file's action (bmdp-tool) or choice (PRISM) index; -1 for an added self-loop */
+  imdp_spec spec;    /* the query the file states; spec.reach and spec.avoid point into this object */
+} imdp_file;
+
+/* Read a bmdp-tool file. *out is library-owned: free it with imdp_file_free. */
+IMDP_API imdp_status imdp_read_bmdp_tool(const char* path, imdp_file** out);
+
+/* Write a model (the CSC arrays of imdp_create_csc, host pointers) and its
+ * terminal states as a bmdp-tool file; the action of column j of state s is
+ * j - stateptr[s]. */
+IMDP_API imdp_status imdp_write_bmdp_tool(const char* path, int32_t n_states, int32_t n_cols, const int32_t* stateptr,
+                                 const int32_t* colptr, const int32_t* rowval, const double* lower,
+                                 const double* upper, const int32_t* terminal, int32_t n_terminal);
+
+/* Read the PRISM explicit files path_stem.{sta,lab,tra,pctl}. *out is
+ * library-owned: free it with imdp_file_free. */
+IMDP_API imdp_status imdp_read_prism(const char* path_stem, imdp_file** out);
+
+/* Write a model (host CSC arrays) and a reachability or reach-avoid
+ * specification as PRISM explicit files path_stem.{sta,lab,tra,pctl}. State 0
+ * is labelled "init"; the target set is labelled "reach" and the avoid set
+ * "avoid". spec->eps is not stored (the format has no place for it). */
+IMDP_API imdp_status imdp_write_prism(const char* path_stem, int32_t n_states, int32_t n_cols, const int32_t* stateptr,
+                             const int32_t* colptr, const int32_t* rowval, const double* lower,
+                             const double* upper, const imdp_spec* spec);
+
+/* Free an imdp_file returned by a read. NULL is ignored. */
+IMDP_API void imdp_file_free(imdp_file* f);
 
 #ifdef __cplusplus
 }

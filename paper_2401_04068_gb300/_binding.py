@@ -15,12 +15,12 @@ import numpy as np
 from . import build as _build
 
 IMDP_OK, IMDP_EINVAL, IMDP_EINFEASIBLE, IMDP_ENOMEM, IMDP_EDEVICE = 0, 1, 2, 3, 4
-IMDP_ETIMEOUT, IMDP_EBUSY, IMDP_ENOCONV, IMDP_ENOTFOUND, IMDP_EPENDING = 5, 6, 7, 8, 9
+IMDP_ETIMEOUT, IMDP_EBUSY, IMDP_ENOCONV, IMDP_ENOTFOUND, IMDP_EPENDING, IMDP_EIO = 5, 6, 7, 8, 9, 10
 IMDP_F64, IMDP_F32 = 0, 1
 IMDP_REACH, IMDP_REACH_AVOID, IMDP_REWARD = 0, 1, 2
 
 STATUS_NAMES = {0: "ok", 1: "einval", 2: "einfeasible", 3: "enomem", 4: "edevice", 5: "etimeout", 6: "ebusy",
-                7: "enoconv", 8: "enotfound", 9: "epending"}
+                7: "enoconv", 8: "enotfound", 9: "epending", 10: "eio"}
 
 # Every symbol include/imdp.h declares (checked by the tests).
 EXPORTED = [
@@ -31,6 +31,7 @@ EXPORTED = [
     "imdp_server_create", "imdp_server_submit", "imdp_server_poll", "imdp_server_wait", "imdp_server_destroy",
     "imdp_model_error_bound", "imdp_partition_states", "imdp_create_csc_slice", "imdp_session_values_get",
     "imdp_session_values_put", "imdp_model_plan", "imdp_debug_stall_producer",
+    "imdp_read_bmdp_tool", "imdp_write_bmdp_tool", "imdp_read_prism", "imdp_write_prism", "imdp_file_free",
 ]
 
 
@@ -54,6 +55,21 @@ class imdp_spec(C.Structure):
         ("n_avoid", C.c_int32),
         ("reward", C.POINTER(C.c_double)),
         ("discount", C.c_double),
+    ]
+
+
+class imdp_file(C.Structure):
+    _fields_ = [
+        ("n_states", C.c_int32),
+        ("n_cols", C.c_int32),
+        ("nnz", C.c_int64),
+        ("stateptr", C.POINTER(C.c_int32)),
+        ("colptr", C.POINTER(C.c_int32)),
+        ("rowval", C.POINTER(C.c_int32)),
+        ("lower", C.POINTER(C.c_double)),
+        ("upper", C.POINTER(C.c_double)),
+        ("action", C.POINTER(C.c_int32)),
+        ("spec", imdp_spec),
     ]
 
 
@@ -121,6 +137,14 @@ def load(path: Optional[str] = None):
     lib.imdp_create_csc_slice.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64, vp, vp, vp, vp, vp,
                                           C.c_int, vp, C.POINTER(vp)]
     lib.imdp_create_csc_slice.restype = C.c_int
+    lib.imdp_read_bmdp_tool.argtypes = [C.c_char_p, C.POINTER(C.POINTER(imdp_file))]
+    lib.imdp_read_prism.argtypes = [C.c_char_p, C.POINTER(C.POINTER(imdp_file))]
+    lib.imdp_write_bmdp_tool.argtypes = [C.c_char_p, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp, C.c_int32]
+    lib.imdp_write_prism.argtypes = [C.c_char_p, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, C.POINTER(imdp_spec)]
+    for f in ("imdp_read_bmdp_tool", "imdp_read_prism", "imdp_write_bmdp_tool", "imdp_write_prism"):
+        getattr(lib, f).restype = C.c_int
+    lib.imdp_file_free.argtypes = [C.POINTER(imdp_file)]
+    lib.imdp_file_free.restype = None
     for f in ("imdp_session_values_get", "imdp_session_values_put"):
         getattr(lib, f).argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, vp]
         getattr(lib, f).restype = C.c_int
@@ -499,3 +523,77 @@ def imdp_model_plan(model: Model):
 def imdp_debug_stall_producer(on: bool):
     """Test hook: step launches leave every consumer wait unsatisfied (see include/imdp.h)."""
     load().imdp_debug_stall_producer(1 if on else 0)
+
+
+# ---------------------------------------------------------------- model files (Sec. 3.1)
+
+class FileModel:
+    """A model read from a file: the CSC arrays ``create_model`` takes, the file's
+    action (choice) index of every column (-1 for an added absorbing self-loop),
+    and ``spec``: keyword arguments for ``make_spec`` / ``value_iteration``."""
+
+    def __init__(self, n_states, stateptr, colptr, rowval, lower, upper, action, spec):
+        self.n_states = n_states
+        self.stateptr, self.colptr, self.rowval = stateptr, colptr, rowval
+        self.lower, self.upper, self.action = lower, upper, action
+        self.spec = spec
+
+
+def _path(p) -> bytes:
+    return os.fsencode(os.fspath(p))
+
+
+def _take_file(fp) -> FileModel:
+    f = fp.contents
+    n, m, nnz = f.n_states, f.n_cols, f.nnz
+
+    def arr(ptr, count, dtype):
+        return np.ctypeslib.as_array(ptr, shape=(count,)).astype(dtype, copy=True) if count else np.zeros(0, dtype)
+
+    sp = f.spec
+    spec = dict(property=sp.property, infinite_time=bool(sp.infinite_time), horizon=sp.horizon, eps=sp.eps,
+                pessimistic=bool(sp.pessimistic), maximize=bool(sp.maximize),
+                reach=arr(sp.reach, sp.n_reach, np.int32), avoid=arr(sp.avoid, sp.n_avoid, np.int32))
+    out = FileModel(n, arr(f.stateptr, n + 1, np.int32), arr(f.colptr, m + 1, np.int32),
+                    arr(f.rowval, nnz, np.int32), arr(f.lower, nnz, np.float64), arr(f.upper, nnz, np.float64),
+                    arr(f.action, m, np.int32), spec)
+    load().imdp_file_free(fp)
+    return out
+
+
+def imdp_read_bmdp_tool(path) -> FileModel:
+    """Read a bmdp-tool file (see include/imdp.h for the layout)."""
+    fp = C.POINTER(imdp_file)()
+    _check(load().imdp_read_bmdp_tool(_path(path), C.byref(fp)), "imdp_read_bmdp_tool")
+    return _take_file(fp)
+
+
+def imdp_read_prism(path_stem) -> FileModel:
+    """Read PRISM explicit files path_stem.{sta,lab,tra,pctl}."""
+    fp = C.POINTER(imdp_file)()
+    _check(load().imdp_read_prism(_path(path_stem), C.byref(fp)), "imdp_read_prism")
+    return _take_file(fp)
+
+
+def _csc_args(m):
+    arrs = [np.ascontiguousarray(m.stateptr, np.int32), np.ascontiguousarray(m.colptr, np.int32),
+            np.ascontiguousarray(m.rowval, np.int32), np.ascontiguousarray(m.lower, np.float64),
+            np.ascontiguousarray(m.upper, np.float64)]
+    return arrs, [a.ctypes.data for a in arrs]
+
+
+def imdp_write_bmdp_tool(path, m, terminal):
+    """Write model ``m`` (CSC arrays) and its terminal states as a bmdp-tool file."""
+    arrs, ptrs = _csc_args(m)
+    t = np.ascontiguousarray(terminal, np.int32)
+    _check(load().imdp_write_bmdp_tool(_path(path), int(m.n_states), len(arrs[1]) - 1, *ptrs,
+                                       t.ctypes.data if t.size else None, int(t.size)), "imdp_write_bmdp_tool")
+
+
+def imdp_write_prism(path_stem, m, **spec_kw):
+    """Write model ``m`` and a reachability / reach-avoid query (``make_spec``
+    keywords) as PRISM explicit files path_stem.{sta,lab,tra,pctl}."""
+    arrs, ptrs = _csc_args(m)
+    spec = make_spec(**spec_kw)
+    _check(load().imdp_write_prism(_path(path_stem), int(m.n_states), len(arrs[1]) - 1, *ptrs, C.byref(spec)),
+           "imdp_write_prism")

@@ -75,6 +75,7 @@ const char* imdp_status_string(imdp_status s) {
     case IMDP_ENOCONV: return "not converged";
     case IMDP_ENOTFOUND: return "not found";
     case IMDP_EPENDING: return "pending";
+    case IMDP_EIO: return "file input/output error";
   }
   return "unknown status";
 }

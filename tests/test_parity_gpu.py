@@ -264,6 +264,23 @@ def test_cta_shapes_agree_to_the_bit():
     np.testing.assert_array_equal(outs[1], wa)
 
 
+def test_models_read_from_files(tmp_path):
+    # the Sec. 3.1 model as PRISM explicit files (with its Sec. 3.2 query) and a
+    # bmdp-tool round trip of a random model, run through the CUDA path
+    import os
+    f = g.imdp_read_prism(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "worked_example"))
+    model = _model(f)
+    st, V, k, res, _ = g.value_iteration(model, f.n_states, **f.spec)
+    _, oV, ok, _, _ = run_oracle(f, **f.spec)
+    assert st == "ok" and k == ok == 100
+    np.testing.assert_allclose(V, oV, rtol=0, atol=TOL_F64)
+    m = random_imdp(300, max_actions=3, seed=93)
+    g.imdp_write_bmdp_tool(tmp_path / "m.bmdp", m, m.goal)
+    fb = g.imdp_read_bmdp_tool(tmp_path / "m.bmdp")
+    spec = dict(fb.spec, horizon=30)
+    _compare(fb, _model(fb), **spec)
+
+
 def test_device_inputs():
     import torch
     m = banded_imdp(200, 2, 200 * 2 * 12 + 1, seed=12)
