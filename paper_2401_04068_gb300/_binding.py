@@ -544,21 +544,22 @@ def _path(p) -> bytes:
 
 
 def _take_file(fp) -> FileModel:
-    f = fp.contents
-    n, m, nnz = f.n_states, f.n_cols, f.nnz
-
+    """Copy a library-owned imdp_file into numpy arrays and free it."""
     def arr(ptr, count, dtype):
         return np.ctypeslib.as_array(ptr, shape=(count,)).astype(dtype, copy=True) if count else np.zeros(0, dtype)
 
-    sp = f.spec
-    spec = dict(property=sp.property, infinite_time=bool(sp.infinite_time), horizon=sp.horizon, eps=sp.eps,
-                pessimistic=bool(sp.pessimistic), maximize=bool(sp.maximize),
-                reach=arr(sp.reach, sp.n_reach, np.int32), avoid=arr(sp.avoid, sp.n_avoid, np.int32))
-    out = FileModel(n, arr(f.stateptr, n + 1, np.int32), arr(f.colptr, m + 1, np.int32),
-                    arr(f.rowval, nnz, np.int32), arr(f.lower, nnz, np.float64), arr(f.upper, nnz, np.float64),
-                    arr(f.action, m, np.int32), spec)
-    load().imdp_file_free(fp)
-    return out
+    try:
+        f = fp.contents
+        n, m, nnz = f.n_states, f.n_cols, f.nnz
+        sp = f.spec
+        spec = dict(property=sp.property, infinite_time=bool(sp.infinite_time), horizon=sp.horizon, eps=sp.eps,
+                    pessimistic=bool(sp.pessimistic), maximize=bool(sp.maximize),
+                    reach=arr(sp.reach, sp.n_reach, np.int32), avoid=arr(sp.avoid, sp.n_avoid, np.int32))
+        return FileModel(n, arr(f.stateptr, n + 1, np.int32), arr(f.colptr, m + 1, np.int32),
+                         arr(f.rowval, nnz, np.int32), arr(f.lower, nnz, np.float64), arr(f.upper, nnz, np.float64),
+                         arr(f.action, m, np.int32), spec)
+    finally:
+        load().imdp_file_free(fp)
 
 
 def imdp_read_bmdp_tool(path) -> FileModel:
