@@ -183,7 +183,7 @@ def _stream(stream) -> Optional[int]:
 
 def _check(status: int, where: str):
     if status != IMDP_OK:
-        raise ImdpError(status, where, load().imdp_last_error().decode())
+        raise ImdpError(status, where, load().imdp_last_error().decode(errors="replace"))
 
 
 def imdp_status_string(status: int) -> str:
@@ -191,7 +191,7 @@ def imdp_status_string(status: int) -> str:
 
 
 def imdp_last_error() -> str:
-    return load().imdp_last_error().decode()
+    return load().imdp_last_error().decode(errors="replace")
 
 
 def imdp_version() -> str:

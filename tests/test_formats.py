@@ -305,3 +305,42 @@ def test_writers_reject_what_the_formats_cannot_hold(tmp_path):
     with pytest.raises(g.ImdpError) as e:
         g.imdp_write_bmdp_tool(tmp_path / "t.bmdp", m, [6])
     assert _status(e) == g.IMDP_EINVAL
+
+
+def test_mutated_fixtures_are_read_or_rejected(tmp_path):
+    # byte-level mutations of the hand-written files: every one is either read
+    # into arrays that satisfy the CSC structure or rejected with a status
+    # (never a crash), and error text is always returned
+    import random
+    rng = random.Random(7)
+    exts = ["bmdp", "sta", "lab", "tra", "pctl"]
+    base = {e: open(os.path.join(GOLDEN, "worked_example." + e), "rb").read() for e in exts}
+    alphabet = b" \t\n\r0123456789.-+e[],:=\"!()FUPRmaxin<>?/" + bytes([0, 128, 255])
+    accepted = 0
+    for _ in range(600):
+        which = rng.choice(exts)
+        for e in exts:
+            b = bytearray(base[e])
+            if e == which:
+                for _ in range(rng.randint(1, 5)):
+                    op = rng.randrange(3)
+                    if op == 0 and b:
+                        del b[rng.randrange(len(b))]
+                    elif op == 1:
+                        b.insert(rng.randrange(len(b) + 1), rng.choice(alphabet))
+                    elif b:
+                        b[rng.randrange(len(b))] = rng.choice(alphabet)
+            (tmp_path / f"f.{e}").write_bytes(bytes(b))
+        try:
+            f = g.imdp_read_bmdp_tool(tmp_path / "f.bmdp") if which == "bmdp" else g.imdp_read_prism(tmp_path / "f")
+        except g.ImdpError as e:
+            assert e.status in (g.IMDP_EINVAL, g.IMDP_ENOMEM) and str(e)
+            continue
+        accepted += 1
+        sp, cp, rv = f.stateptr, f.colptr, f.rowval
+        assert sp[0] == 0 and np.all(np.diff(sp) >= 1) and sp[-1] == len(cp) - 1
+        assert cp[0] == 0 and np.all(np.diff(cp) >= 1) and cp[-1] == len(rv)
+        assert np.all((rv >= 0) & (rv < f.n_states))
+        assert all(np.all(np.diff(rv[cp[j]:cp[j + 1]]) > 0) for j in range(len(cp) - 1))
+        assert np.all(np.isfinite(f.lower)) and np.all(np.isfinite(f.upper))
+    assert 0 < accepted < 600
