@@ -294,6 +294,25 @@ IMDP_API imdp_status imdp_session_values_put(imdp_session* s, int32_t index, int
                                              const uint64_t* src, void* stream);
 
 /*
+ * Checkpoint and resume (not in the paper: value iteration's whole state for one
+ * problem is its iterate V_k and k). imdp_session_checkpoint copies problem
+ * `index`'s latest iterate (n_states raw 64-bit words as imdp_session_values_get
+ * gives them) to `raw_V` (host or device) and its completed iterations to *k.
+ * imdp_session_restore writes both into problem `index` of a session built from
+ * the same model and specification, which then continues with iteration k + 1
+ * (a finite horizon with k = horizon is finished). The problem's threshold hints
+ * start empty after a restore, so a resumed run matches an uninterrupted one
+ * within the arithmetic's rounding (1e-13 in V), not bit for bit; rows of a
+ * time-dependent policy computed before the checkpoint are not part of it. Both
+ * calls are ordered on `stream` and synchronize it. IMDP_EINVAL for a bad
+ * index, k < 0, k above a finite horizon, or NULL pointers.
+ */
+IMDP_API imdp_status imdp_session_checkpoint(imdp_session* s, int32_t index, uint64_t* raw_V, int32_t* k,
+                                             void* stream);
+IMDP_API imdp_status imdp_session_restore(imdp_session* s, int32_t index, const uint64_t* raw_V, int32_t k,
+                                          void* stream);
+
+/*
  * Continuous-batching server. Requests (a resident model plus a specification)
  * share the Bellman launches of one slotted batch run by a worker thread: a
  * request is admitted when a slot (up to 1024) and enough of the server's device

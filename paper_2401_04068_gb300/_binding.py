@@ -32,6 +32,7 @@ EXPORTED = [
     "imdp_model_error_bound", "imdp_partition_states", "imdp_create_csc_slice", "imdp_session_values_get",
     "imdp_session_values_put", "imdp_model_plan", "imdp_debug_stall_producer",
     "imdp_read_bmdp_tool", "imdp_write_bmdp_tool", "imdp_read_prism", "imdp_write_prism", "imdp_file_free",
+    "imdp_session_checkpoint", "imdp_session_restore",
 ]
 
 
@@ -143,6 +144,10 @@ def load(path: Optional[str] = None):
     lib.imdp_write_prism.argtypes = [C.c_char_p, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, C.POINTER(imdp_spec)]
     for f in ("imdp_read_bmdp_tool", "imdp_read_prism", "imdp_write_bmdp_tool", "imdp_write_prism"):
         getattr(lib, f).restype = C.c_int
+    lib.imdp_session_checkpoint.argtypes = [vp, C.c_int32, vp, C.POINTER(C.c_int32), vp]
+    lib.imdp_session_checkpoint.restype = C.c_int
+    lib.imdp_session_restore.argtypes = [vp, C.c_int32, vp, C.c_int32, vp]
+    lib.imdp_session_restore.restype = C.c_int
     lib.imdp_file_free.argtypes = [C.POINTER(imdp_file)]
     lib.imdp_file_free.restype = None
     for f in ("imdp_session_values_get", "imdp_session_values_put"):
@@ -484,6 +489,23 @@ def imdp_create_csc_slice(n_states: int, s0: int, s1: int, n_cols: int, nnz: int
                                       _stream(stream), C.byref(out))
     _check(st, "imdp_create_csc_slice")
     return Model(out.value)
+
+
+def imdp_session_checkpoint(s: Session, index: int, raw_out=None, stream=None):
+    """(raw iterate, k) of problem ``index``; ``raw_out`` may be a host array or a
+    CUDA tensor of n_states uint64 words (allocated on the host when None)."""
+    if raw_out is None:
+        raw_out = np.zeros(s._models[index].info()["n_states"], np.uint64)
+    k = C.c_int32(0)
+    _check(load().imdp_session_checkpoint(C.c_void_p(s.handle), int(index), _ptr(raw_out), C.byref(k),
+                                          _stream(stream)), "imdp_session_checkpoint")
+    return raw_out, k.value
+
+
+def imdp_session_restore(s: Session, index: int, raw, k: int, stream=None):
+    """Write a checkpoint (raw iterate, k) into problem ``index``."""
+    _check(load().imdp_session_restore(C.c_void_p(s.handle), int(index), _ptr(raw), int(k), _stream(stream)),
+           "imdp_session_restore")
 
 
 def imdp_session_values_get(s: Session, index: int, k: int, s0: int, s1: int, dst, stream=None):

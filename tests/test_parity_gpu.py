@@ -281,6 +281,50 @@ def test_models_read_from_files(tmp_path):
     _compare(fb, _model(fb), **spec)
 
 
+def test_checkpoint_and_resume():
+    # stop a run after k1 iterations, restore (V_k1, k1) into a fresh session and
+    # finish there: the same V as the uninterrupted run (hints start empty after
+    # a restore, so within rounding rather than bitwise) and the oracle's V
+    import torch
+    m = banded_imdp(400, 2, 400 * 2 * 30 + 1, seed=94)
+    model = _model(m)
+    for spec_kw, k1 in [(dict(horizon=40, reach=m.goal), 15),
+                        (dict(horizon=35, reach=m.goal, pessimistic=False, maximize=False), 35),
+                        (dict(infinite_time=True, eps=1e-9, horizon=100000, reach=m.goal), 20)]:
+        spec = g.make_spec(**spec_kw)
+        full = g.imdp_session_create([model], [spec])
+        g.imdp_session_run(full)
+        V_full, k_full = np.zeros(m.n_states), [0]
+        g.imdp_session_read(full, 0, V_full, k_full)
+
+        first = g.imdp_session_create([model], [spec])
+        g.imdp_session_step(first, k1)
+        raw, k = g.imdp_session_checkpoint(first, 0)
+        assert k == k1
+        dev = torch.zeros(m.n_states, dtype=torch.int64, device="cuda")
+        _, kd = g.imdp_session_checkpoint(first, 0, dev)  # device buffer: the same words
+        assert kd == k1 and np.array_equal(dev.cpu().numpy().view(np.uint64), raw)
+
+        second = g.imdp_session_create([model], [spec])
+        g.imdp_session_restore(second, 0, raw, k)
+        g.imdp_session_run(second)
+        V, kk = np.zeros(m.n_states), [0]
+        g.imdp_session_read(second, 0, V, kk)
+        if spec_kw.get("infinite_time"):
+            assert abs(kk[0] - k_full[0]) <= 1
+        else:
+            assert kk[0] == k_full[0] == spec_kw["horizon"]
+        np.testing.assert_allclose(V, V_full, rtol=0, atol=1e-13)
+        _, oV, _, _, _ = run_oracle(m, **spec_kw)
+        np.testing.assert_allclose(V, oV, rtol=0, atol=TOL_F64 if not spec_kw.get("infinite_time") else 1e-8)
+    # bad arguments
+    s = g.imdp_session_create([model], [g.make_spec(horizon=10, reach=m.goal)])
+    raw = np.zeros(m.n_states, np.uint64)
+    for idx, kk in [(1, 0), (0, 11), (0, -1)]:
+        with pytest.raises(g.ImdpError):
+            g.imdp_session_restore(s, idx, raw, kk)
+
+
 def test_device_inputs():
     import torch
     m = banded_imdp(200, 2, 200 * 2 * 12 + 1, seed=12)
