@@ -28,6 +28,18 @@ def lib_path():
     return pbuild.build()
 
 
+def _declared_statuses():
+    text = open(os.path.join(ROOT, "include", "imdp.h")).read()
+    return {name: int(v) for name, v in re.findall(r"\b(IMDP_E[A-Z]+|IMDP_OK)\s*=\s*(\d+)", text)}
+
+
+def test_binding_status_codes_match_the_header():
+    declared = _declared_statuses()
+    assert sorted(declared.values()) == sorted(pkg.STATUS_NAMES)
+    for name, v in declared.items():
+        assert getattr(pkg, name) == v, name
+
+
 def test_header_declares_the_boundary():
     names = _declared_functions()
     for must in ("imdp_create_csc", "imdp_value_iteration", "imdp_value_iteration_batch", "imdp_model_destroy"):
@@ -51,6 +63,10 @@ def test_loads_and_reports_status_strings(lib_path):
     lib = pkg.load()
     assert pkg.imdp_status_string(0) == "ok"
     assert pkg.imdp_status_string(2) == "infeasible interval model"
+    # every status the header defines has its own name in the library and the binding
+    names = {pkg.imdp_status_string(c) for c in pkg.STATUS_NAMES}
+    assert len(names) == len(pkg.STATUS_NAMES) and "unknown status" not in names
+    assert pkg.imdp_status_string(pkg.IMDP_EIO) == "file input/output error"
     assert pkg.imdp_version().count(".") == 2
     assert lib is pkg.load()
 
