@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "imdp_internal.h"
@@ -52,6 +53,9 @@ class Lexer {
  public:
   Lexer(const std::string& text, std::string name)
       : p_(text.c_str()), end_(text.c_str() + text.size()), name_(std::move(name)) {}
+  // The part [begin, end) of a NUL-terminated text, whose first line is `line`.
+  Lexer(const char* begin, const char* end, std::string name, int64_t line)
+      : p_(begin), end_(end), name_(std::move(name)), line_(line) {}
 
   // Skip blanks; newlines too when `lines`.
   void skip(bool lines) {
@@ -143,7 +147,8 @@ class Lexer {
     return p_ < end_ ? *p_ : '\0';
   }
   std::string where() const { return name_ + ":" + std::to_string(line_); }
-  int32_t line() const { return line_ > INT32_MAX ? INT32_MAX : (int32_t)line_; }
+  int64_t line64() const { return line_; }
+  const char* pos() const { return p_; }
 
  private:
   bool ends_token(const char* e) const {
@@ -195,11 +200,12 @@ void free_file(imdp_file* f) {
 // give a state without transitions one absorbing column; copy the arrays out.
 imdp_status assemble(const std::string& name, int32_t n, std::vector<Entry>& es, bool dense_choices,
                      std::vector<int32_t> reach, std::vector<int32_t> avoid, const imdp_spec& spec, imdp_file** out) {
-  std::sort(es.begin(), es.end(), [](const Entry& x, const Entry& y) {
+  const auto csc_order = [](const Entry& x, const Entry& y) {
     if (x.s != y.s) return x.s < y.s;
     if (x.a != y.a) return x.a < y.a;
     return x.d < y.d;
-  });
+  };
+  if (!std::is_sorted(es.begin(), es.end(), csc_order)) std::sort(es.begin(), es.end(), csc_order);
   std::vector<int32_t> sp, cp, rv, act;
   std::vector<double> lo, up;
   sp.reserve((size_t)n + 1);
@@ -337,12 +343,153 @@ struct Out {
   void put(const char* text) {
     if (ok && std::fputs(text, f) < 0) ok = false;
   }
+  void write(const std::string& text) {
+    if (ok && !text.empty() && std::fwrite(text.data(), 1, text.size(), f) != text.size()) ok = false;
+  }
   bool close() {
     if (f && std::fclose(f) != 0) ok = false;
     f = nullptr;
     return ok;
   }
 };
+
+// ---------------------------------------------------------------- host threads
+//
+// Reading and writing large models is bound by number parsing and formatting
+// (strtod / snprintf, a few hundred ns per bound), so both run on all host
+// cores: the text is cut at line starts into one part per thread, and the
+// parts are joined in file order.
+
+unsigned host_threads(size_t bytes) {
+  if (bytes < ((size_t)1 << 20)) return 1;  // small files: not worth a thread
+  const unsigned hc = std::thread::hardware_concurrency();
+  return std::max(1u, std::min(hc ? hc : 1u, 16u));
+}
+
+// f(i) for i in [0, n), on up to n threads; f must not throw. A thread that
+// cannot be started runs its part on the calling thread.
+template <class F>
+void run_parts(unsigned n, F&& f) {
+  std::vector<std::thread> th;
+  for (unsigned i = 1; i < n; ++i) {
+    try {
+      th.emplace_back(f, i);
+    } catch (...) {
+      f(i);
+    }
+  }
+  f(0);
+  for (auto& t : th) t.join();
+}
+
+// Parse the entry lines of [body, end of text) with `one` (reads one entry from a
+// lexer standing on its first token, or sets a message and returns false). The
+// first error in file order is reported with its line in the whole file; the
+// entries come back in file order. `body_line` is the line `body` lies on.
+template <class One>
+imdp_status parse_body(const std::string& text, const char* body, int64_t body_line, const std::string& name,
+                       One one, std::vector<Entry>* out) {
+  const char* end = text.c_str() + text.size();
+  const unsigned T = host_threads((size_t)(end - body));
+  std::vector<const char*> cut(T + 1);
+  cut[0] = body;
+  cut[T] = end;
+  for (unsigned i = 1; i < T; ++i) {
+    const char* c = std::max(cut[i - 1], body + (size_t)(end - body) * i / T);
+    const char* nl = static_cast<const char*>(std::memchr(c, '\n', (size_t)(end - c)));
+    cut[i] = nl ? nl + 1 : end;
+  }
+  struct Part {
+    std::vector<Entry> es;
+    int64_t newlines = 0;
+    bool bad = false, oom = false;
+    int64_t bad_line = 0;
+    std::string msg;
+  };
+  std::vector<Part> parts(T);
+  run_parts(T, [&](unsigned i) {
+    Part& P = parts[i];
+    try {
+      Lexer lx(cut[i], cut[i + 1], name, 1);
+      while (!lx.at_end()) {
+        Entry e{};
+        const int64_t ln = lx.line64();
+        if (!one(lx, &e, &P.msg)) {
+          P.bad = true;
+          P.bad_line = lx.line64();
+          return;
+        }
+        e.line = (int32_t)std::min<int64_t>(ln, INT32_MAX);  // local for now
+        P.es.push_back(e);
+      }
+      P.newlines = lx.line64() - 1;
+    } catch (...) {
+      P.bad = P.oom = true;
+    }
+  });
+  int64_t base = body_line;  // line of each part's first character
+  size_t total = 0;
+  for (unsigned i = 0; i < T; ++i) {
+    Part& P = parts[i];
+    if (P.oom) throw std::bad_alloc();
+    if (P.bad) return parse_error(name + ":" + std::to_string(base + P.bad_line - 1), P.msg);
+    for (Entry& e : P.es) e.line = (int32_t)std::min<int64_t>(base + e.line - 1, INT32_MAX);
+    base += P.newlines;
+    total += P.es.size();
+  }
+  out->clear();
+  out->reserve(total);
+  for (Part& P : parts) {
+    out->insert(out->end(), P.es.begin(), P.es.end());
+    std::vector<Entry>().swap(P.es);
+  }
+  return IMDP_OK;
+}
+
+// Write one line per stored transition, `fmt(buf, cap, s, action, e)` giving the
+// text of entry e (column action of state s). States are taken in blocks of
+// about kBlockEntries entries; the blocks of a round are formatted in parallel
+// and written in order.
+constexpr int64_t kBlockEntries = 1 << 18;
+
+template <class Fmt>
+void write_entry_lines(Out& o, int32_t n, const int32_t* sp, const int32_t* cp, Fmt fmt) {
+  std::vector<int32_t> starts{0};
+  int64_t acc = 0;
+  for (int32_t s = 0; s < n; ++s) {
+    acc += cp[sp[s + 1]] - cp[sp[s]];
+    if (acc >= kBlockEntries) {
+      starts.push_back(s + 1);
+      acc = 0;
+    }
+  }
+  if (starts.back() != n) starts.push_back(n);
+  const size_t blocks = starts.size() - 1;
+  const unsigned T = host_threads((size_t)cp[sp[n]] * 40);
+  for (size_t w = 0; w < blocks && o.ok; w += T) {
+    const unsigned wn = (unsigned)std::min<size_t>(T, blocks - w);
+    std::vector<std::string> bufs(wn);
+    std::vector<char> failed(wn, 0);
+    run_parts(wn, [&](unsigned b) {
+      try {
+        std::string& text = bufs[b];
+        char line[160];
+        for (int32_t s = starts[w + b]; s < starts[w + b + 1]; ++s)
+          for (int32_t j = sp[s]; j < sp[s + 1]; ++j)
+            for (int32_t e = cp[j]; e < cp[j + 1]; ++e) {
+              const int k = fmt(line, sizeof(line), s, j - sp[s], e);
+              if (k > 0) text.append(line, (size_t)std::min<int>(k, (int)sizeof(line) - 1));
+            }
+      } catch (...) {
+        failed[b] = 1;
+      }
+    });
+    for (unsigned b = 0; b < wn; ++b) {
+      if (failed[b]) throw std::bad_alloc();
+      o.write(bufs[b]);
+    }
+  }
+}
 
 imdp_status io_error(const std::string& path) {
   set_error("cannot write " + path);
@@ -474,18 +621,30 @@ IMDP_API imdp_status imdp_read_bmdp_tool(const char* path, imdp_file** out) {
       term[(size_t)i] = (int32_t)t;
     }
     std::vector<Entry> es;
-    while (!lx.at_end()) {
+    imdp_status st = parse_body(text, lx.pos(), lx.line64(), path, [&](Lexer& l, Entry* e, std::string* msg) {
       int64_t s = -1, a = -1, d = -1;
       double lo = 0, up = 0;
-      const int32_t line = lx.line();
-      if (!lx.integer(&s) || !lx.integer(&a, false) || !lx.integer(&d, false) || !lx.number(&lo, false) ||
-          !lx.number(&up, false) || !lx.at_eol())
-        return parse_error(lx.where(), "expected: source action destination lower upper");
-      if (s < 0 || s >= n || d < 0 || d >= n) return parse_error(lx.where(), "state index out of range");
-      if (a < 0 || a >= na) return parse_error(lx.where(), "action index out of range [0, n_actions)");
-      if (!finite_bounds(lo, up)) return parse_error(lx.where(), "bounds must be finite numbers");
-      es.push_back(Entry{(int32_t)s, (int32_t)a, (int32_t)d, line, lo, up});
-    }
+      if (!l.integer(&s) || !l.integer(&a, false) || !l.integer(&d, false) || !l.number(&lo, false) ||
+          !l.number(&up, false) || !l.at_eol()) {
+        *msg = "expected: source action destination lower upper";
+        return false;
+      }
+      if (s < 0 || s >= n || d < 0 || d >= n) {
+        *msg = "state index out of range";
+        return false;
+      }
+      if (a < 0 || a >= na) {
+        *msg = "action index out of range [0, n_actions)";
+        return false;
+      }
+      if (!finite_bounds(lo, up)) {
+        *msg = "bounds must be finite numbers";
+        return false;
+      }
+      *e = Entry{(int32_t)s, (int32_t)a, (int32_t)d, 0, lo, up};
+      return true;
+    }, &es);
+    if (st != IMDP_OK) return st;
     imdp_spec spec = default_spec();
     return assemble(path, (int32_t)n, es, false, std::move(term), {}, spec, out);
   });
@@ -516,10 +675,9 @@ IMDP_API imdp_status imdp_write_bmdp_tool(const char* path, int32_t n_states, in
     Out o(path);
     o.print("%d\n%d\n%d\n", n_states, na, n_terminal);
     for (int32_t i = 0; i < n_terminal; ++i) o.print("%d\n", terminal[i]);
-    for (int32_t s = 0; s < n_states && o.ok; ++s)
-      for (int32_t j = stateptr[s]; j < stateptr[s + 1]; ++j)
-        for (int32_t e = colptr[j]; e < colptr[j + 1]; ++e)
-          o.print("%d %d %d %.17g %.17g\n", s, j - stateptr[s], rowval[e], lower[e], upper[e]);
+    write_entry_lines(o, n_states, stateptr, colptr, [&](char* buf, size_t cap, int32_t s, int32_t a, int32_t e) {
+      return std::snprintf(buf, cap, "%d %d %d %.17g %.17g\n", s, a, rowval[e], lower[e], upper[e]);
+    });
     return o.close() ? IMDP_OK : io_error(path);
   });
 }
@@ -548,19 +706,30 @@ IMDP_API imdp_status imdp_read_prism(const char* path_stem, imdp_file** out) {
         !lt.integer(&t, false) || t < 0 || t >= INT32_MAX || !lt.at_eol())
       return parse_error(lt.where(), "expected: n_states n_choices n_transitions");
     std::vector<Entry> es;
-    es.reserve(std::min<size_t>((size_t)t, tra.size() / 8 + 1));  // a line takes at least 8 characters
-    while (!lt.at_end()) {
+    imdp_status pst = parse_body(tra, lt.pos(), lt.line64(), stem + ".tra", [&](Lexer& l, Entry* e, std::string* msg) {
       int64_t s = -1, c = -1, d = -1;
       double lo = 0, up = 0;
-      const int32_t line = lt.line();
-      if (!lt.integer(&s) || !lt.integer(&c, false) || !lt.integer(&d, false) || !lt.interval(&lo, &up))
-        return parse_error(lt.where(), "expected: source choice destination [lower,upper]");
-      lt.next_line();  // an action name may follow
-      if (s < 0 || s >= n || d < 0 || d >= n) return parse_error(lt.where(), "state index out of range");
-      if (c < 0 || c >= std::max<int64_t>(m, 1)) return parse_error(lt.where(), "choice index out of range");
-      if (!finite_bounds(lo, up)) return parse_error(lt.where(), "bounds must be finite numbers");
-      es.push_back(Entry{(int32_t)s, (int32_t)c, (int32_t)d, line, lo, up});
-    }
+      if (!l.integer(&s) || !l.integer(&c, false) || !l.integer(&d, false) || !l.interval(&lo, &up)) {
+        *msg = "expected: source choice destination [lower,upper]";
+        return false;
+      }
+      l.next_line();  // an action name may follow
+      if (s < 0 || s >= n || d < 0 || d >= n) {
+        *msg = "state index out of range";
+        return false;
+      }
+      if (c < 0 || c >= std::max<int64_t>(m, 1)) {
+        *msg = "choice index out of range";
+        return false;
+      }
+      if (!finite_bounds(lo, up)) {
+        *msg = "bounds must be finite numbers";
+        return false;
+      }
+      *e = Entry{(int32_t)s, (int32_t)c, (int32_t)d, 0, lo, up};
+      return true;
+    }, &es);
+    if (pst != IMDP_OK) return pst;
     if ((int64_t)es.size() != t)
       return parse_error(stem + ".tra", "header gives " + std::to_string(t) + " transitions, the file has " +
                                             std::to_string(es.size()));
@@ -715,10 +884,9 @@ IMDP_API imdp_status imdp_write_prism(const char* path_stem, int32_t n_states, i
     {
       Out o(stem + ".tra");
       o.print("%d %d %d\n", n_states, n_cols, colptr[n_cols]);
-      for (int32_t s = 0; s < n_states && o.ok; ++s)
-        for (int32_t j = stateptr[s]; j < stateptr[s + 1]; ++j)
-          for (int32_t e = colptr[j]; e < colptr[j + 1]; ++e)
-            o.print("%d %d %d [%.17g,%.17g]\n", s, j - stateptr[s], rowval[e], lower[e], upper[e]);
+      write_entry_lines(o, n_states, stateptr, colptr, [&](char* buf, size_t cap, int32_t s, int32_t c, int32_t e) {
+        return std::snprintf(buf, cap, "%d %d %d [%.17g,%.17g]\n", s, c, rowval[e], lower[e], upper[e]);
+      });
       if (!o.close()) return io_error(stem + ".tra");
     }
     {

@@ -344,3 +344,36 @@ def test_mutated_fixtures_are_read_or_rejected(tmp_path):
         assert all(np.all(np.diff(rv[cp[j]:cp[j + 1]]) > 0) for j in range(len(cp) - 1))
         assert np.all(np.isfinite(f.lower)) and np.all(np.isfinite(f.upper))
     assert 0 < accepted < 600
+
+
+def test_large_files_are_read_in_parts_in_file_order(tmp_path):
+    # files above 1 MB are parsed on several host threads: arrays, order and the
+    # line number of an error deep in the file must not depend on that
+    import random
+    from workloads import banded_imdp
+    m = banded_imdp(3000, 2, 3000 * 2 * 20 + 1, seed=95)
+    p = tmp_path / "big.bmdp"
+    g.imdp_write_bmdp_tool(p, m, m.goal)
+    assert os.path.getsize(p) > (4 << 20)
+    _same_arrays(g.imdp_read_bmdp_tool(p), m)
+    lines = open(p).read().splitlines()
+    header, body = lines[:3 + len(m.goal)], lines[3 + len(m.goal):]
+    random.Random(1).shuffle(body)  # any line order reads back the same
+    p.write_text("\n".join(header + body) + "\n")
+    _same_arrays(g.imdp_read_bmdp_tool(p), m)
+    bad = len(lines) - 1234  # 0-based index of a line near the end
+    lines[bad] = "0 0 x 0.5 0.5"
+    p.write_text("\n".join(lines) + "\n")
+    with pytest.raises(g.ImdpError) as e:
+        g.imdp_read_bmdp_tool(p)
+    assert f"big.bmdp:{bad + 1}:" in str(e.value)
+
+    g.imdp_write_prism(tmp_path / "big", m, horizon=50, reach=m.goal)
+    _same_arrays(g.imdp_read_prism(tmp_path / "big"), m)
+    tra = open(tmp_path / "big.tra").read().splitlines()
+    bad = len(tra) // 2 + 7
+    tra[bad] = tra[bad].replace("[", "(")
+    (tmp_path / "big.tra").write_text("\n".join(tra) + "\n")
+    with pytest.raises(g.ImdpError) as e:
+        g.imdp_read_prism(tmp_path / "big")
+    assert f"big.tra:{bad + 1}:" in str(e.value)
