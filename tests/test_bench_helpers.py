@@ -1,5 +1,6 @@
 """Bookkeeping of bench.py on the CPU: algorithmic bytes, the traffic record's
-source-hash check, and the whole-job timing reduction at one rank."""
+source-hash check, the whole-job timing reduction at one rank, and the
+reference arm's JSON line."""
 import json
 import os
 
@@ -39,3 +40,24 @@ def test_committed_traffic_record_is_well_formed():
     for name, r in rec.items():
         assert len(r["source_hash"]) == 16 and r["dram_bytes_per_launch"] > 0
     assert np.isfinite(bench.measured_peak_hbm()[0])
+
+
+def test_reference_arm_prints_the_contract_line():
+    # bench.py --impl reference runs the oracle on the host: one JSON line with the
+    # keys the measurement contract names (a small batch and budget keep it short)
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--models", "32", "--ref-budget", "0.5"],
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["config"]["workload"] == "pendulum240_x4096" and d["config"]["models"] == 32
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
