@@ -80,3 +80,27 @@ def test_product_path_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".h", ".cuh")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text and "imdp_oracle" not in text, f
+
+
+def test_plain_c_client(lib_path, tmp_path):
+    # include/imdp.h compiles as strict C99, and a C program links the library and
+    # uses the host-only calls (no GPU): bmdp-tool read, write, read back
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path / "abi_client")
+    libdir = os.path.dirname(lib_path)
+    libname = os.path.basename(lib_path)[3:-3]  # libNAME.so -> NAME
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "abi_client.c"), "-L", libdir, f"-l{libname}",
+                    f"-Wl,-rpath,{libdir}", "-o", exe], check=True, capture_output=True, text=True)
+    out = subprocess.run([exe, os.path.join(ROOT, "tests", "golden", "worked_example.bmdp"),
+                          str(tmp_path / "copy.bmdp")], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stdout + out.stderr
+    text = out.stdout
+    assert f"version {pkg.imdp_version()}" in text
+    assert "status infeasible interval model" in text
+    assert "model 3 states 5 columns 13 transitions, terminal 2" in text
+    assert "round trip same" in text
+    assert "missing file: file input/output error\n" in text
