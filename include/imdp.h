@@ -161,12 +161,14 @@ IMDP_API imdp_status imdp_model_error_bound(const imdp_model* m, double* per_ite
  * NULL. IMDP_EINVAL for a NULL model. */
 IMDP_API imdp_status imdp_model_plan(const imdp_model* m, int32_t* n_tiles, int32_t* n_wide, int64_t* wide_entries);
 
-/* Test hook for failure detection (no counterpart in the paper). While `on` is
- * nonzero, step launches of the tiled kernel issue no tile copies: every
- * consumer wait runs into its bound (about 2 s), the kernel records the error
- * and returns, and the next read of the session reports IMDP_ETIMEOUT; the
- * CUDA context stays usable (reset the session and run again). Process-wide;
- * not for production use. */
+/* TEST-ONLY hook for failure detection (no counterpart in the paper; never
+ * call it in production code). While `on` is nonzero, step launches of the
+ * tiled kernel issue no tile copies: every consumer wait runs into its bound
+ * (about 2 s), the kernel records the error and returns, and the next read of
+ * the session reports IMDP_ETIMEOUT; the CUDA context stays usable. The switch
+ * is process-wide; imdp_session_reset turns it off again (and drops the
+ * session's captured graph, which may hold stalled launches), so a session
+ * that is reset after a timeout runs normally. */
 IMDP_API void imdp_debug_stall_producer(int32_t on);
 
 /*
@@ -210,7 +212,8 @@ IMDP_API imdp_status imdp_value_iteration_batch(imdp_model* const* models, const
  *   V_out     double[n_states], DEVICE memory on the model's device (current)
  *   k_out     (host, nullable) iterations performed
  * The first call on a device looks up the scratch array's device address; make
- * that first call before any stream capture. All calls share the one array:
+ * that first call before any stream capture. Every call synchronizes `stream`
+ * before it returns (it reads the iteration state back). All calls share the one array:
  * calls that overlap on the GPU (other streams or host threads) race. Policy and
  * residual outputs are not offered here.
  */
@@ -303,7 +306,12 @@ IMDP_API imdp_status imdp_session_values_put(imdp_session* s, int32_t index, int
  * (a finite horizon with k = horizon is finished). The problem's threshold hints
  * start empty after a restore, so a resumed run matches an uninterrupted one
  * within the arithmetic's rounding (1e-13 in V), not bit for bit; rows of a
- * time-dependent policy computed before the checkpoint are not part of it. Both
+ * time-dependent policy computed before the checkpoint are not part of it. The
+ * session may have run before the restore (it need not be fresh): the next
+ * imdp_session_run still carries the restored problem to its horizon. A
+ * checkpoint does not record that an infinite-horizon problem had already
+ * converged (only V_k and k are kept), so such a problem, restored, runs one
+ * more iteration before its convergence test stops it again (k + 1). Both
  * calls are ordered on `stream` and synchronize it. IMDP_EINVAL for a bad
  * index, k < 0, k above a finite horizon, or NULL pointers.
  */

@@ -6,7 +6,8 @@ imports this package and shares no code with it.
 
 ``imdp_oracle.c`` holds the arithmetic (value iteration, Eq. 2; O-maximization,
 Sec. 4, sequential procedure).  This module compiles it with gcc and wraps it
-with ctypes.  ``exact.py`` holds the exact-rational checker used to pin it.
+with ctypes.  The exact-rational checker that pins it lives with the tests
+(``tests/exact_lp.py``).
 """
 from .oracle import (  # noqa: F401
     OracleIMDP,

@@ -6,6 +6,7 @@
 // iteration k + 1.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "imdp_internal.h"
@@ -98,6 +99,11 @@ IMDP_API imdp_status imdp_session_restore(imdp_session* s, int32_t index, const 
     e = cudaMemsetAsync(P.hint, 0xff, sizeof(int32_t) * padded_i32((size_t)S->models[index]->n_cols), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // `it` lives on this stack frame
   if (e != cudaSuccess) return cuda_status(e, "restore");
+  // The session's launch count since its reset bounds how many more launches
+  // imdp_session_run issues; a problem restored to iteration k needs up to
+  // horizon - k more, whatever the session ran before (extra launches skip
+  // finished problems on the device).
+  S->launched_since_reset = std::min<int64_t>(S->launched_since_reset, k);
   return IMDP_OK;
 }
 

@@ -217,6 +217,7 @@ struct Session {
   StepLaunch L{};
   int grid = 1;
   cudaGraphExec_t graph = nullptr;
+  bool graph_stalled = false;  // captured while the failure-detection test hook was on
   int64_t launches = 0;
   int64_t launched_since_reset = 0;
   std::vector<void*> allocs;

@@ -285,6 +285,13 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
 
 imdp_status Session::reset(cudaStream_t st) {
   TraceRange trace("imdp session reset");
+  // the failure-detection test hook ends with a reset; a graph captured while it
+  // was on replays launches that issue no copies, so it is captured again
+  g_stall_producer.store(0);
+  if (graph && graph_stalled) {
+    cudaGraphExecDestroy(graph);
+    graph = nullptr;
+  }
   init_values_kernel<<<(int)std::min<int64_t>((total + 255) / 256, 8192), 256, 0, st>>>(total, fixed, V);
   cudaError_t e = cudaGetLastError();
   for (int p = 0; p < count && e == cudaSuccess; ++p)
@@ -312,6 +319,7 @@ imdp_status Session::step(int32_t n, cudaStream_t st) {
   if (st != nullptr && n >= kGraphChunk) {
     if (!graph) {
       cudaGraph_t g = nullptr;
+      graph_stalled = g_stall_producer.load() != 0;
       e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
       for (int i = 0; i < kGraphChunk && e == cudaSuccess; ++i) e = launch_bellman_step(L, grid, st, &side);
       cudaError_t e2 = cudaStreamEndCapture(st, &g);

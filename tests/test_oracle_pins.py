@@ -425,3 +425,38 @@ def test_invalid_spec():
     assert oracle.value_iteration(m, oracle.OracleSpec(property=oracle.REWARD, reward=np.ones(5), discount=1.5))[0] == "einval"
     # non-convergence within the iteration cap is reported
     assert oracle.value_iteration(m, oracle.OracleSpec(infinite_time=True, eps=1e-300, horizon=5, reach=[4]))[0] == "enoconv"
+
+
+# --------------------------------------------------------------------------- threaded sweep
+
+@pytest.mark.parametrize("kind", ["finite", "infinite", "reward", "reach_avoid"])
+def test_threaded_sweep_gives_the_same_words(kind):
+    # The OpenMP sweep splits the states of one Bellman iteration over threads
+    # (Sec. 4: the per-state problems are independent within an iteration) and
+    # combines only the residual, by a max. Every state is computed by the same
+    # sequential code whatever thread runs it, so 1, 2 and 8 threads must give
+    # the same binary64 words, the same k and the same policy.
+    if not oracle.has_openmp():
+        pytest.skip("oracle built without OpenMP")
+    m = banded_imdp(700, 3, 700 * 3 * 25 + 1, eps=0.1, seed=77)
+    kw = dict(reach=m.goal)
+    if kind == "finite":
+        sp = oracle.OracleSpec(horizon=40, pessimistic=True, maximize=True, **kw)
+    elif kind == "infinite":
+        sp = oracle.OracleSpec(infinite_time=True, eps=1e-9, horizon=100000, pessimistic=False, maximize=True, **kw)
+    elif kind == "reward":
+        r = np.random.default_rng(3).random(m.n_states)
+        sp = oracle.OracleSpec(property=oracle.REWARD, horizon=30, reward=r, discount=0.9, pessimistic=True,
+                               maximize=False)
+    else:
+        avoid = np.setdiff1d(np.arange(0, m.n_states, 37), m.goal)
+        sp = oracle.OracleSpec(property=oracle.REACH_AVOID, horizon=30, avoid=avoid, pessimistic=True,
+                               maximize=True, **kw)
+    ref = oracle.value_iteration(_om(m), sp, policy=True, threads=1)
+    assert ref[0] == "ok"
+    for t in (2, 8):
+        got = oracle.value_iteration(_om(m), sp, policy=True, threads=t)
+        assert got[0] == ref[0] and got[2] == ref[2]
+        assert np.array_equal(got[1].view(np.uint64), ref[1].view(np.uint64))
+        assert np.array_equal(got[3].view(np.uint64), ref[3].view(np.uint64))
+        assert np.array_equal(got[4], ref[4])

@@ -325,6 +325,27 @@ def test_checkpoint_and_resume():
             g.imdp_session_restore(s, idx, raw, kk)
 
 
+def test_restore_into_a_session_that_already_ran():
+    # A restore may target a session that has stepped or run before: the next
+    # run must still carry the restored problem from k to its horizon (Eq. 2
+    # iterations k + 1 .. K), not stop at the session's earlier launch count.
+    m = banded_imdp(300, 2, 300 * 2 * 20 + 1, seed=96)
+    model = _model(m)
+    spec = g.make_spec(horizon=30, reach=m.goal)
+    s = g.imdp_session_create([model], [spec])
+    g.imdp_session_step(s, 10)
+    raw, k = g.imdp_session_checkpoint(s, 0)
+    assert k == 10
+    g.imdp_session_run(s)  # to the horizon
+    g.imdp_session_restore(s, 0, raw, k)
+    g.imdp_session_run(s)
+    V, kk = np.zeros(m.n_states), [0]
+    assert g.imdp_session_read(s, 0, V, kk) == g.IMDP_OK and kk[0] == 30
+    _, oV, _, _, _ = run_oracle(m, horizon=30, reach=m.goal)
+    np.testing.assert_allclose(V, oV, rtol=0, atol=TOL_F64)
+    s.close()
+
+
 def test_device_inputs():
     import torch
     m = banded_imdp(200, 2, 200 * 2 * 12 + 1, seed=12)
@@ -492,7 +513,7 @@ def test_reward_batch_mixed_with_reachability():
 def test_wide_intervals_sum_of_upper_far_above_one(k_mean, n_dom):
     # upper = 1 on every entry: a column's upper bounds add up to k (gap sums
     # far beyond 2 in fixed point); the last case has columns longer than a
-    # shared-memory tile (read from global memory)
+    # shared-memory tile, which run as wide states in the block-wide kernel
     m = banded_imdp(n_dom, 1, n_dom * (k_mean + 1) + 1, eps=0.1, seed=k_mean)
     m.upper = np.ones_like(m.upper)
     m.lower = m.lower * 0.5

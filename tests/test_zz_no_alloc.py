@@ -81,3 +81,41 @@ def test_noalloc_with_wide_states_matches_regular():
         # takes the full search, whose products are truncated in another grouping
         # than the warm start's: equal up to K * k_max * 2^-62 (~2e-14 here)
         np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=1e-13)
+
+
+def test_noalloc_against_the_oracle_directly():
+    # The same query answered by the allocation-free entry point and by the CPU
+    # oracle (binary64, Eq. 2 with the Sec. 4 procedure), element by element.
+    import torch
+    from gpu_helpers import run_oracle
+    m = banded_imdp(1500, 3, 1500 * 3 * 25 + 1500 * 3 + 1, eps=0.1, seed=35)
+    model = g.create_model(m)
+    for kw in (dict(horizon=50, pessimistic=True, maximize=True),
+               dict(horizon=40, pessimistic=False, maximize=False)):
+        out = torch.full((m.n_states,), -1.0, dtype=torch.float64, device="cuda")
+        k = [0]
+        assert g.imdp_value_iteration_noalloc(model, g.make_spec(reach=m.goal, **kw), out, k) == g.IMDP_OK
+        st, oV, ok, _, _ = run_oracle(m, reach=m.goal, **kw)
+        assert st == "ok" and k[0] == ok == kw["horizon"]
+        np.testing.assert_allclose(out.cpu().numpy(), oV, rtol=0, atol=TOL_F64)
+
+
+def test_noalloc_32bit_storage_model():
+    # A model with 32-bit bound storage through the allocation-free entry point:
+    # the regular entry point's answer (same stored bounds; threshold hints
+    # differ, so equal within the 64-bit products' truncation) and the oracle
+    # within the model's a-priori storage bound.
+    import torch
+    from gpu_helpers import run_oracle
+    m = banded_imdp(800, 2, 800 * 2 * 30 + 800 * 2 + 1, eps=0.1, seed=36)
+    model = g.create_model(m, dtype=g.IMDP_F32)
+    K = 40
+    spec = g.make_spec(horizon=K, reach=m.goal)
+    ref = np.zeros(m.n_states)
+    g.imdp_value_iteration(model, spec, ref)
+    out = torch.zeros(m.n_states, dtype=torch.float64, device="cuda")
+    assert g.imdp_value_iteration_noalloc(model, spec, out) == g.IMDP_OK
+    got = out.cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+    _, oV, _, _, _ = run_oracle(m, horizon=K, reach=m.goal)
+    assert float(np.max(np.abs(got - oV))) <= K * model.error_bound() + TOL_F64
