@@ -257,6 +257,50 @@ IMDP_API int64_t imdp_session_launches(const imdp_session* s);
 IMDP_API void imdp_session_destroy(imdp_session* s);
 
 /*
+ * Launch configuration of a session's Bellman step (no counterpart in the
+ * paper, whose GPU kernels have one fixed shape). Every configuration computes
+ * the same words; they differ in speed only. Zero fields mean "by rule".
+ *   kernel        0 by rule (ring); 1 ring: a producer warp bulk-copies tiles of
+ *                 consecutive states into a three-stage shared-memory ring for
+ *                 consumer warps; 2 direct: every warp takes the next tile and
+ *                 streams its columns from global memory itself
+ *   cta_warps     ring: 16 or 24 warps per CTA (24 only without wide states; rule:
+ *                 24 when the tiles hold 16 or more columns on average); direct: 8
+ *   ctas_per_sm   direct: 3 or 4 (rule 4); ring: 1
+ *   tile_entries  tile plan: at most this many transitions per tile, 1..3072
+ *                 (rule 3072; a single state may exceed a smaller limit)
+ *   wide_col      a state with a column of this many transitions or more (or
+ *                 more than 3072 transitions in all) runs in the block-wide
+ *                 kernel (rule 1280)
+ */
+typedef struct {
+  int32_t kernel;
+  int32_t cta_warps;
+  int32_t ctas_per_sm;
+  int32_t tile_entries;
+  int32_t wide_col;
+} imdp_launch_config;
+/* Use `cfg` from the next step on. A changed tile plan is rebuilt (this waits
+ * for `stream`); the session's captured graph is dropped. Problems keep their
+ * state, so a configuration may change between steps. IMDP_EINVAL for NULL. */
+IMDP_API imdp_status imdp_session_set_launch(imdp_session* s, const imdp_launch_config* cfg, void* stream);
+/* The configuration the session's launches use, with every field resolved by
+ * the rule where the set configuration left it open. */
+IMDP_API imdp_status imdp_session_get_launch(const imdp_session* s, imdp_launch_config* cfg);
+/*
+ * Autotuner. Times candidate launch configurations on this session (each: a
+ * reset, then `iters` Bellman iterations, timed with CUDA events on `stream`
+ * after one untimed run) and keeps the fastest. The choice is cached in the
+ * JSON file `cache_path` (nullable: no cache) under a key describing the
+ * session's shape (storage, mean transitions per column, columns per state,
+ * states, whether it has wide states); a later call with the same key applies
+ * the cached configuration without timing. The session is reset afterwards.
+ * `chosen` (nullable) receives the configuration in use; `ms_per_iter`
+ * (nullable) its measured time per iteration (0 when taken from the cache).
+ */
+IMDP_API imdp_status imdp_session_autotune(imdp_session* s, int32_t iters, const char* cache_path, void* stream,
+                                           imdp_launch_config* chosen, double* ms_per_iter);
+/*
  * State-sharded value iteration (one model split over several GPUs).
  * Sec. 4 notes that the per-state problems of Eq. 2 are independent within an
  * iteration: a slice that owns states [s0, s1) computes V_k[s0, s1) exactly as

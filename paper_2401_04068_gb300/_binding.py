@@ -33,7 +33,24 @@ EXPORTED = [
     "imdp_session_values_put", "imdp_model_plan", "imdp_debug_stall_producer",
     "imdp_read_bmdp_tool", "imdp_write_bmdp_tool", "imdp_read_prism", "imdp_write_prism", "imdp_file_free",
     "imdp_session_checkpoint", "imdp_session_restore",
+    "imdp_session_set_launch", "imdp_session_get_launch", "imdp_session_autotune",
 ]
+
+
+class imdp_launch_config(C.Structure):
+    _fields_ = [
+        ("kernel", C.c_int32),
+        ("cta_warps", C.c_int32),
+        ("ctas_per_sm", C.c_int32),
+        ("tile_entries", C.c_int32),
+        ("wide_col", C.c_int32),
+    ]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+KERNEL_RULE, KERNEL_RING, KERNEL_DIRECT = 0, 1, 2
 
 
 class ImdpError(RuntimeError):
@@ -107,6 +124,10 @@ def load(path: Optional[str] = None):
     lib.imdp_value_iteration_batch.argtypes = [C.POINTER(vp), C.POINTER(imdp_spec), C.c_int32, C.POINTER(vp),
                                                C.POINTER(C.c_int32), vp]
     lib.imdp_session_create.argtypes = [C.POINTER(vp), C.POINTER(imdp_spec), C.c_int32, vp, vp, C.POINTER(vp)]
+    lib.imdp_session_set_launch.argtypes = [vp, C.POINTER(imdp_launch_config), vp]
+    lib.imdp_session_get_launch.argtypes = [vp, C.POINTER(imdp_launch_config)]
+    lib.imdp_session_autotune.argtypes = [vp, C.c_int32, C.c_char_p, vp, C.POINTER(imdp_launch_config),
+                                          C.POINTER(C.c_double)]
     lib.imdp_session_reset.argtypes = [vp, vp]
     lib.imdp_session_step.argtypes = [vp, C.c_int32, vp]
     lib.imdp_session_run.argtypes = [vp, C.c_int32, vp]
@@ -365,6 +386,32 @@ def imdp_session_launches(s: Session) -> int:
 
 def imdp_session_destroy(s: Session):
     s.close()
+
+
+def imdp_session_set_launch(s: Session, kernel: int = 0, cta_warps: int = 0, ctas_per_sm: int = 0,
+                            tile_entries: int = 0, wide_col: int = 0, stream=None):
+    """Launch configuration of the session's Bellman step (0 fields: by rule)."""
+    cfg = imdp_launch_config(kernel, cta_warps, ctas_per_sm, tile_entries, wide_col)
+    _check(load().imdp_session_set_launch(C.c_void_p(s.handle), C.byref(cfg), _stream(stream)),
+           "imdp_session_set_launch")
+
+
+def imdp_session_get_launch(s: Session) -> dict:
+    """The resolved launch configuration of the session."""
+    cfg = imdp_launch_config()
+    _check(load().imdp_session_get_launch(C.c_void_p(s.handle), C.byref(cfg)), "imdp_session_get_launch")
+    return cfg.as_dict()
+
+
+def imdp_session_autotune(s: Session, iters: int, cache_path: Optional[str] = None, stream=None):
+    """Time the candidate launch configurations (or take the cached choice) and
+    keep the fastest. Returns (configuration dict, ms per iteration; 0 when cached)."""
+    cfg = imdp_launch_config()
+    ms = C.c_double(0.0)
+    _check(load().imdp_session_autotune(C.c_void_p(s.handle), int(iters),
+                                        cache_path.encode() if cache_path else None, _stream(stream),
+                                        C.byref(cfg), C.byref(ms)), "imdp_session_autotune")
+    return cfg.as_dict(), float(ms.value)
 
 
 def imdp_value_iteration_noalloc(model: Model, spec, V_out, k_out=None, stream=None, check=True) -> int:

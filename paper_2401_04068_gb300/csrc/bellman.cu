@@ -231,18 +231,63 @@ __device__ __forceinline__ uint64_t warp_excl_scan_sat(uint64_t x, int lane) {
 // through L1). `hint` is the entry that held the threshold in the previous
 // iteration (-1: none); the entry that holds it now is returned in *hint_out.
 // Returns q in Q2.62.
+//
+// Loads from global memory: a column's destinations and bounds are read once
+// per pass and streamed (L1 evict-first), the values V_{k-1} are gathered by
+// many columns and kept (L1 evict-last). All of them are read-only during a
+// launch (V_k goes to the other buffer), so the non-coherent path is used. The
+// asm is volatile so that the compiler never executes a load speculatively
+// ahead of the bounds test that guards it (entries past a column's end may lie
+// past the end of the array).
+__device__ __forceinline__ int32_t ld_stream_i32(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.global.nc.L1::evict_first.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ ulonglong2 ld_stream_u64x2(const ulonglong2* p) {
+  ulonglong2 v;
+  asm volatile("ld.global.nc.L1::evict_first.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_stream_u32x2(const uint2* p) {
+  uint2 v;
+  asm volatile("ld.global.nc.L1::evict_first.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_value(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.global.nc.L1::evict_last.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+
+// Destinations of one column in global memory (streamed loads); in shared
+// memory a plain pointer serves.
+struct GRows {
+  const int32_t* p;
+  __device__ __forceinline__ int32_t operator[](int idx) const { return ld_stream_i32(p + idx); }
+};
+template <bool gmem>
+struct RowsOf {
+  typedef const int32_t* type;
+};
+template <>
+struct RowsOf<true> {
+  typedef GRows type;
+};
+
 // Bounds of one column as {lower, gap} in Q1.63, from 64-bit storage or from
-// 32-bit mantissas shifted up by `down` = 32 - shift_j.
-template <bool f32>
+// 32-bit mantissas shifted up by `down` = 32 - shift_j; `gmem`: the pairs are
+// in global memory (streamed loads), else in shared memory.
+template <bool f32, bool gmem = false>
 struct Bounds {
   const void* p;
   int down;
   __device__ __forceinline__ ulonglong2 operator[](int idx) const {
     if (f32) {
-      const uint2 m = static_cast<const uint2*>(p)[idx];
+      const uint2 m = gmem ? ld_stream_u32x2(static_cast<const uint2*>(p) + idx) : static_cast<const uint2*>(p)[idx];
       return make_ulonglong2((uint64_t)m.x << down, (uint64_t)m.y << down);
     }
-    return static_cast<const ulonglong2*>(p)[idx];
+    return gmem ? ld_stream_u64x2(static_cast<const ulonglong2*>(p) + idx) : static_cast<const ulonglong2*>(p)[idx];
   }
 };
 
@@ -252,8 +297,8 @@ struct Bounds {
 // and contribute zero. With `carry` the per-lane gap sums count their wraps and
 // saturate; without it the column is narrow (all its gaps add up to < 2^64), so
 // no sum can wrap.
-template <bool carry, bool f32>
-__device__ __forceinline__ void warm_pass(const int32_t* rows, const Bounds<f32> lg, int32_t k,
+template <bool carry, bool f32, bool gmem>
+__device__ __forceinline__ void warm_pass(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k,
                                           const uint64_t* __restrict__ V, uint64_t vk, bool pess, int lane,
                                           uint64_t& acc, uint64_t& flt, uint64_t& geq) {
   uint32_t fc = 0, gc = 0;
@@ -262,7 +307,7 @@ __device__ __forceinline__ void warm_pass(const int32_t* rows, const Bounds<f32>
   for (int it = 0; it < nb; ++it) {
     const int idx = it * 32 + lane;
     const bool ok = idx < k;
-    const uint64_t v = __ldg(V + (ok ? rows[idx] : 0));
+    const uint64_t v = ld_value(V + (ok ? rows[idx] : 0));
     const ulonglong2 b = ok ? lg[idx] : make_ulonglong2(0, 0);
     const bool below = pess ? (v < vk) : (v > vk);
     acc += __umul64hi(v, b.x + (below ? b.y : 0ull));
@@ -301,8 +346,8 @@ struct WarmMiss {
   bool valid;
 };
 
-template <bool f32>
-__device__ __forceinline__ bool column_warm(const int32_t* rows, const Bounds<f32> lg, int32_t k, uint64_t rem_word,
+template <bool f32, bool gmem>
+__device__ __forceinline__ bool column_warm(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem_word,
                                             const uint64_t* __restrict__ V, bool pess, int lane, int32_t hint,
                                             uint64_t* q, WarmMiss* miss) {
   miss->valid = false;
@@ -310,20 +355,20 @@ __device__ __forceinline__ bool column_warm(const int32_t* rows, const Bounds<f3
   if (rem == 0) {
     uint64_t acc = 0;
 #pragma unroll 4
-    for (int idx = lane; idx < k; idx += 32) acc += __umul64hi(__ldg(V + rows[idx]), lg[idx].x);
+    for (int idx = lane; idx < k; idx += 32) acc += __umul64hi(ld_value(V + rows[idx]), lg[idx].x);
     *q = warp_sum_u64(acc);
     return true;
   }
   if (hint < 0 || hint >= k) return false;
-  const uint64_t vk = __ldg(V + rows[hint]);
+  const uint64_t vk = ld_value(V + rows[hint]);
   uint64_t acc = 0, flt = 0, geq = 0;
   if (narrow_of(rem_word)) {
     // every gap sum of a narrow column is below 2^64: plain exact sums
-    warm_pass<false>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
+    warm_pass<false, f32, gmem>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
     flt = warp_sum_u64(flt);
     geq = warp_sum_u64(geq);
   } else {
-    warm_pass<true>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
+    warm_pass<true, f32, gmem>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
     flt = warp_sum_sat(flt);
     geq = warp_sum_sat(geq);
   }
@@ -346,8 +391,8 @@ __device__ __forceinline__ bool column_warm(const int32_t* rows, const Bounds<f3
 //   above: F(< kappa+) = F(<= kappa), holds when F(<= kappa) + G >= rem;
 // and q is the warm formula at the new key, to the bit. Returns false when the
 // threshold moved further (or a sum is not exact), leaving the full search.
-template <bool f32>
-__device__ __forceinline__ bool column_neighbor(const int32_t* rows, const Bounds<f32> lg, int32_t k, uint64_t rem,
+template <bool f32, bool gmem>
+__device__ __forceinline__ bool column_neighbor(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem,
                                                 const uint64_t* __restrict__ V, bool pess, int lane,
                                                 const WarmMiss& w, uint64_t* q, int32_t* hint_out) {
   const bool down = w.flt >= rem;
@@ -360,7 +405,7 @@ __device__ __forceinline__ bool column_neighbor(const int32_t* rows, const Bound
   for (int it = 0; it < nb; ++it) {
     const int idx = it * 32 + lane;
     if (idx >= k) break;
-    const uint64_t v = __ldg(V + rows[idx]);
+    const uint64_t v = ld_value(V + rows[idx]);
     const uint64_t key = pess ? v : kOne - v;
     const ulonglong2 b = lg[idx];
     const uint64_t d = __umul64hi(v, b.x + b.y) - __umul64hi(v, b.x);
@@ -405,13 +450,13 @@ __device__ __forceinline__ bool column_neighbor(const int32_t* rows, const Bound
 
 // Threshold search over a column with rem > 0 (the warm start failed or had no
 // hint). Returns q in Q2.62 and the threshold entry in *hint_out.
-template <bool f32>
-__device__ uint64_t column_search(const int32_t* rows, const Bounds<f32> lg, int32_t k, uint64_t rem_word,
+template <bool f32, bool gmem>
+__device__ uint64_t column_search(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem_word,
                                   const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane,
                                   int32_t* hint_out) {
   const uint64_t rem = rem_of(rem_word);
   auto key_of = [&](int idx) -> uint64_t {
-    const uint64_t v = __ldg(V + rows[idx]);
+    const uint64_t v = ld_value(V + rows[idx]);
     return pess ? v : (kOne - v);
   };
 
@@ -577,8 +622,8 @@ __device__ uint64_t column_search(const int32_t* rows, const Bounds<f32> lg, int
 }
 
 // One column, warm start first: q in Q2.62, the threshold entry in *hint_out.
-template <bool f32>
-__device__ uint64_t column_q(const int32_t* rows, const Bounds<f32> lg, int32_t k, uint64_t rem_word,
+template <bool f32, bool gmem>
+__device__ uint64_t column_q(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem_word,
                              const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane, int32_t hint,
                              int32_t* hint_out) {
   // A hint of -2 - i names entry i as well and records that the column's last
@@ -588,15 +633,15 @@ __device__ uint64_t column_q(const int32_t* rows, const Bounds<f32> lg, int32_t 
   const int32_t entry = moving ? -2 - hint : hint;
   uint64_t q;
   WarmMiss miss;
-  if (column_warm<f32>(rows, lg, k, rem_word, V, pess, lane, entry, &q, &miss)) {
+  if (column_warm<f32, gmem>(rows, lg, k, rem_word, V, pess, lane, entry, &q, &miss)) {
     *hint_out = entry;
     return q;
   }
   if (miss.valid && !moving &&
-      column_neighbor<f32>(rows, lg, k, rem_of(rem_word), V, pess, lane, miss, &q, hint_out))
+      column_neighbor<f32, gmem>(rows, lg, k, rem_of(rem_word), V, pess, lane, miss, &q, hint_out))
     return q;
   int32_t found;
-  q = column_search<f32>(rows, lg, k, rem_word, V, pess, ws, lane, &found);
+  q = column_search<f32, gmem>(rows, lg, k, rem_word, V, pess, ws, lane, &found);
   *hint_out = found >= 0 ? -2 - found : -1;
   return q;
 }
@@ -643,6 +688,19 @@ __device__ __forceinline__ void best_action(const Problem& P, int32_t jb, int32_
   *best = bb;
 }
 
+// V_k(s) of a free state from the optimum over its actions (Q2.62): the
+// reachability value clamped at 1, or the reward update W_k = c_s + gamma T(W_{k-1})
+// in signed Q2.62, clamped to [0, 1].
+__device__ __forceinline__ uint64_t free_state_value(const Problem& P, int32_t s, uint64_t bestq) {
+  if (P.property == kPropReward) {
+    const int64_t tt = (int64_t)(__umul64hi(P.gamma_fix, bestq) << 1);
+    int64_t w = P.rbias[s] + tt;
+    w = w < 0 ? 0 : (w > (int64_t)(kOne >> 1) ? (int64_t)(kOne >> 1) : w);
+    return (uint64_t)w << 1;
+  }
+  return bestq >= (kOne >> 1) ? kOne : (bestq << 1);  // Q2.62 -> Q1.63, clamp at 1
+}
+
 // State epilogue of a tile (one warp): opt over actions, reach/avoid mask,
 // reward update, V / policy / residual. `fixed_at(s)` gives the mask of state s,
 // `best_of(s, &q, &a)` the optimal action value and index.
@@ -663,15 +721,7 @@ __device__ void tile_epilogue(const StepLaunch& L, const Problem& P, const Tile&
     } else {
       uint64_t bestq;
       best_of(s, &bestq, &best);
-      if (P.property == kPropReward) {
-        // W_k = c_s + gamma * T(W_{k-1}) in signed Q2.62, clamped to [0, 1]
-        const int64_t tt = (int64_t)(__umul64hi(P.gamma_fix, bestq) << 1);
-        int64_t w = P.rbias[s] + tt;
-        w = w < 0 ? 0 : (w > (int64_t)(kOne >> 1) ? (int64_t)(kOne >> 1) : w);
-        vnew = (uint64_t)w << 1;
-      } else {
-        vnew = bestq >= (kOne >> 1) ? kOne : (bestq << 1);  // Q2.62 -> Q1.63, clamp at 1
-      }
+      vnew = free_state_value(P, s, bestq);
     }
     finish_state(P, s, k_iter, vnew, best, Vin, Vout, dmax);
   }
@@ -696,7 +746,7 @@ __device__ __forceinline__ void stage_column(Stage& st, const Tile& T, int32_t l
   else
     bd = Bounds<f32>{st.lg + (ca - T.e0), 0};
   int32_t hout;
-  const uint64_t q = column_q<f32>(st.rows + (ca - eb), bd, ce - ca, st.rem[c - mb], P.V[(k_iter - 1) & 1],
+  const uint64_t q = column_q<f32, false>(st.rows + (ca - eb), bd, ce - ca, st.rem[c - mb], P.V[(k_iter - 1) & 1],
                                    P.pessimistic != 0, ws, lane, h, &hout);
   if (lane == 0) {
     st.q[li] = q;
@@ -903,7 +953,123 @@ __device__ void end_of_launch(const StepLaunch& L, int* is_last) {
   if (threadIdx.x == 0) {
     L.ctl->finished = 0;
     L.ctl->wide_next = 0;
+    L.ctl->tile_next = 0;
   }
+}
+
+
+// ---------------------------------------------------------------- direct kernel
+//
+// The same Bellman step over the same tile list without the shared-memory ring:
+// every warp takes the next tile (atomic counter), streams its columns straight
+// from global memory (destinations and bounds with L1 evict-first loads, the
+// values V_{k-1} with evict-last gathers) and finishes each state itself. There
+// is no producer warp, no barrier and no staging buffer, so the whole L1 holds
+// V_{k-1} and the columns being searched, and as many columns are in flight as
+// there are warps (the ring holds three tiles per SM). Columns of states held
+// fixed by the property (reach / avoid) are not read: Eq. 2 sets those values
+// directly. Each column runs the same exact routines as in the ring kernel,
+// so both kernels give the same words.
+
+// Column metadata of 32 consecutive columns, one per lane.
+struct ColChunk {
+  int32_t base = -1;
+  int32_t ca = 0, ce = 0, hint = -1, shift = 0;
+  uint64_t rem = 0;
+};
+
+template <bool f32>
+__device__ void direct_tile(const StepLaunch& L, const Tile& T, int32_t k_iter, WarpScratch* ws, int lane) {
+  const Problem& P = L.probs[T.p];
+  const uint64_t* __restrict__ Vin = P.V[(k_iter - 1) & 1];
+  uint64_t* __restrict__ Vout = P.V[k_iter & 1];
+  const bool pess = P.pessimistic != 0;
+  const bool maxi = P.maximize != 0;
+  const int32_t* __restrict__ colptr = P.colptr;
+  int32_t* hint = P.hint;
+  unsigned long long dmax = 0;
+  ColChunk cc;
+  for (int32_t sb = T.s0; sb < T.s1; sb += 32) {
+    // per-state metadata, one state per lane
+    const int32_t ms = sb + lane;
+    int32_t m_jb = 0, m_je = 0, m_fx = 0;
+    if (ms < T.s1) {
+      m_jb = __ldg(P.stateptr + ms);
+      m_je = __ldg(P.stateptr + ms + 1);
+      m_fx = __ldg(P.fixed + ms);
+    }
+    const int ns = T.s1 - sb < 32 ? T.s1 - sb : 32;
+    for (int i = 0; i < ns; ++i) {
+      const int32_t s = sb + i;
+      const int32_t fx = __shfl_sync(kFull, m_fx, i);
+      uint64_t vnew;
+      int32_t best = -1;
+      if (fx == 1) {
+        vnew = kOne;
+      } else if (fx == 2) {
+        vnew = 0;
+      } else {
+        const int32_t jb = __shfl_sync(kFull, m_jb, i), je = __shfl_sync(kFull, m_je, i);
+        uint64_t bq = 0;
+        for (int32_t c = jb; c < je; ++c) {
+          if (cc.base < 0 || c - cc.base >= 32) {  // next 32 columns' metadata, one per lane
+            cc.base = c;
+            const int32_t mc = c + lane;
+            if (mc < T.c1) {
+              cc.ca = __ldg(colptr + mc);
+              cc.ce = __ldg(colptr + mc + 1);
+              cc.rem = __ldg(P.rem + mc);
+              cc.hint = hint ? hint[mc] : -1;
+              if (f32) cc.shift = __ldg(P.shift + mc);
+            }
+          }
+          const int src = c - cc.base;
+          const int32_t ca = __shfl_sync(kFull, cc.ca, src), ce = __shfl_sync(kFull, cc.ce, src);
+          const int32_t h = __shfl_sync(kFull, cc.hint, src);
+          const uint64_t rw = __shfl_sync(kFull, cc.rem, src);
+          int32_t hout;
+          uint64_t q;
+          if (f32)
+            q = column_q<true, true>(GRows{P.rowval + ca},
+                                     Bounds<true, true>{P.lg32 + ca, 32 - __shfl_sync(kFull, cc.shift, src)}, ce - ca,
+                                     rw, Vin, pess, ws, lane, h, &hout);
+          else
+            q = column_q<false, true>(GRows{P.rowval + ca}, Bounds<false, true>{P.lg + ca, 0}, ce - ca, rw, Vin, pess,
+                                      ws, lane, h, &hout);
+          if (lane == 0 && hint && hout != h) hint[c] = hout;
+          if (best < 0 || (maxi ? q > bq : q < bq)) {
+            bq = q;
+            best = c - jb;
+          }
+        }
+        vnew = free_state_value(P, s, bq);
+      }
+      if (lane == 0) finish_state(P, s, k_iter, vnew, best, Vin, Vout, dmax);
+    }
+  }
+  if (P.infinite && lane == 0 && dmax) atomicMax(&L.its[T.p].resmax, dmax);
+}
+
+template <int NW, int MINB>
+__global__ void __launch_bounds__(32 * NW, MINB) bellman_direct_kernel(StepLaunch L) {
+  __shared__ WarpScratch ws_all[NW];
+  __shared__ int is_last;
+  const int lane = threadIdx.x & 31;
+  WarpScratch* ws = &ws_all[threadIdx.x >> 5];
+  for (;;) {
+    int32_t t = 0;
+    if (lane == 0) t = (int32_t)atomicAdd(&L.ctl->tile_next, 1u);
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= L.n_tiles) break;
+    const Tile T = L.tiles[t];
+    int32_t k_iter;
+    if (!problem_active(L, T.p, &k_iter)) continue;
+    if (L.probs[T.p].lg32)
+      direct_tile<true>(L, T, k_iter, ws, lane);
+    else
+      direct_tile<false>(L, T, k_iter, ws, lane);
+  }
+  end_of_launch(L, &is_last);
 }
 
 // ---------------------------------------------------------------- wide states
@@ -989,7 +1155,7 @@ __device__ bool wide_neighbor(const int32_t* __restrict__ rows, const Bounds<f32
   int32_t bi = -1;
 #pragma unroll 4
   for (int idx = tid; idx < k; idx += kWideThreads) {
-    const uint64_t v = __ldg(V + rows[idx]);
+    const uint64_t v = ld_value(V + rows[idx]);
     const uint64_t key = pess ? v : kOne - v;
     const ulonglong2 b = lg[idx];
     const uint64_t d = __umul64hi(v, b.x + b.y) - __umul64hi(v, b.x);
@@ -1065,7 +1231,7 @@ __device__ uint64_t wide_search(const int32_t* __restrict__ rows, const Bounds<f
                                 const uint64_t* __restrict__ V, bool pess, int32_t* found, WideShared& W) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   auto key_of = [&](int idx) -> uint64_t {
-    const uint64_t v = __ldg(V + rows[idx]);
+    const uint64_t v = ld_value(V + rows[idx]);
     return pess ? v : (kOne - v);
   };
   uint64_t cmin = ~0ull, cmax = 0;
@@ -1248,18 +1414,18 @@ __device__ uint64_t wide_column_q(const int32_t* __restrict__ rows, const Bounds
   if (rem == 0) {
     uint64_t a = 0, f = 0, g = 0;
 #pragma unroll 4
-  for (int idx = tid; idx < k; idx += kWideThreads) a += __umul64hi(__ldg(V + rows[idx]), lg[idx].x);
+  for (int idx = tid; idx < k; idx += kWideThreads) a += __umul64hi(ld_value(V + rows[idx]), lg[idx].x);
     block_sum3(W, warp, lane, a, f, g);
     *hint_out = entry;
     return a;
   }
   if (entry >= 0 && entry < k) {
-    const uint64_t vk = __ldg(V + rows[entry]);
+    const uint64_t vk = ld_value(V + rows[entry]);
     uint64_t acc = 0, flt = 0, geq = 0;
     uint32_t fc = 0, gc = 0;
 #pragma unroll 4
     for (int idx = tid; idx < k; idx += kWideThreads) {
-      const uint64_t v = __ldg(V + rows[idx]);
+      const uint64_t v = ld_value(V + rows[idx]);
       const ulonglong2 b = lg[idx];
       const bool below = pess ? (v < vk) : (v > vk);
       acc += __umul64hi(v, b.x + (below ? b.y : 0ull));
@@ -1339,14 +1505,7 @@ __global__ void __launch_bounds__(kWideThreads, 6) bellman_wide_kernel(StepLaunc
           best = c - c0;
         }
       }
-      if (P.property == kPropReward) {
-        const int64_t tt = (int64_t)(__umul64hi(P.gamma_fix, bestq) << 1);
-        int64_t wv = P.rbias[s] + tt;
-        wv = wv < 0 ? 0 : (wv > (int64_t)(kOne >> 1) ? (int64_t)(kOne >> 1) : wv);
-        vnew = (uint64_t)wv << 1;
-      } else {
-        vnew = bestq >= (kOne >> 1) ? kOne : (bestq << 1);
-      }
+      vnew = free_state_value(P, s, bestq);
     }
     if (threadIdx.x == 0) {
       unsigned long long dmax = 0;
@@ -1359,14 +1518,17 @@ __global__ void __launch_bounds__(kWideThreads, 6) bellman_wide_kernel(StepLaunc
 
 }  // namespace
 
-void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out, std::vector<int32_t>& wide) {
+void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out, std::vector<int32_t>& wide,
+                int32_t tile_entries, int32_t wide_col) {
   const std::vector<int32_t>& sp = m->h_stateptr;
   const std::vector<int32_t>& cp = m->h_colptr;
   const int32_t n = m->own1;  // owned states only
+  const int32_t te = tile_entries > 0 && tile_entries < kTileEntries ? tile_entries : kTileEntries;
+  const int32_t wc = wide_col > 0 ? wide_col : kWideCol;
   auto is_wide = [&](int32_t s) {
     if (cp[sp[s + 1]] - cp[sp[s]] > kTileEntries || sp[s + 1] - sp[s] > kTileCols) return true;
     for (int32_t c = sp[s]; c < sp[s + 1]; ++c)
-      if (cp[c + 1] - cp[c] >= kWideCol) return true;
+      if (cp[c + 1] - cp[c] >= wc) return true;
     return false;
   };
   int32_t s = m->own0;
@@ -1382,7 +1544,7 @@ void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out, std:
     T.c0 = sp[s];
     T.e0 = cp[sp[s]];
     int32_t t = s + 1;
-    while (t < n && !is_wide(t) && cp[sp[t + 1]] - T.e0 <= kTileEntries && sp[t + 1] - T.c0 <= kTileCols &&
+    while (t < n && !is_wide(t) && cp[sp[t + 1]] - T.e0 <= te && sp[t + 1] - T.c0 <= kTileCols &&
            t + 1 - s <= kTileStates)
       ++t;
     T.s1 = t;
@@ -1402,7 +1564,30 @@ int bellman_grid() {
 
 std::atomic<int> g_stall_producer{0};
 
-cudaError_t launch_bellman_step(const StepLaunch& L0, int grid, cudaStream_t st, const SideStream* side) {
+LaunchConfig resolve_launch(const StepLaunch& L, const LaunchConfig* cfg) {
+  LaunchConfig r;
+  if (cfg) r = *cfg;
+  if (r.kernel != kKernelDirect) r.kernel = kKernelRing;
+  if (r.kernel == kKernelDirect) {
+    r.cta_warps = kDirectWarps;
+    r.ctas_per_sm = r.ctas_per_sm == 3 ? 3 : 4;
+  } else {
+    // 24 warps (23 consumers) for tiles of many short columns; never beside wide
+    // CTAs (a 24-warp CTA leaves no registers for one)
+    const bool can24 = L.n_wide == 0;
+    const bool rule24 = can24 && L.tile_cols >= (int64_t)kShortColsPerTile * L.n_tiles;
+    r.cta_warps = (r.cta_warps == 24 && can24) || (r.cta_warps != 16 && r.cta_warps != 24 && rule24)
+                      ? kConsumersShort + 1
+                      : kConsumersLong + 1;
+    r.ctas_per_sm = 1;
+  }
+  if (r.tile_entries <= 0 || r.tile_entries > kTileEntries) r.tile_entries = kTileEntries;
+  if (r.wide_col <= 0) r.wide_col = kWideCol;
+  return r;
+}
+
+cudaError_t launch_bellman_step(const StepLaunch& L0, int grid, cudaStream_t st, const SideStream* side,
+                                const LaunchConfig* cfg) {
   // per-device setup, once (sessions, servers and the allocation-free entry
   // point may launch from several threads)
   static std::atomic<int> configured[64];
@@ -1431,24 +1616,32 @@ cudaError_t launch_bellman_step(const StepLaunch& L0, int grid, cudaStream_t st,
   }
   StepLaunch L = L0;
   L.stall = g_stall_producer.load(std::memory_order_relaxed);
-  const int mg = L.n_tiles > 0 ? grid : 1;  // one CTA still takes part in the end-of-launch ticket
+  const LaunchConfig rc = resolve_launch(L, cfg);
+  const int kind = rc.kernel;
+  const int direct_per_sm = rc.ctas_per_sm;
+  const bool short_cols = kind == kKernelRing && rc.cta_warps == kConsumersShort + 1;
   const int wg = L.n_wide > 0 ? std::min(L.n_wide, wide_blocks[dev]) : 0;
+  // one CTA still takes part in the end-of-launch ticket when there are no tiles
+  const int mg = L.n_tiles <= 0 ? 1 : (kind == kKernelDirect ? grid * direct_per_sm : grid);
   L.grid_total = mg + wg;
-  // 23 consumer warps for tiles of many short columns; never beside wide CTAs
-  // (a 24-warp CTA leaves no registers for one)
-  const bool short_cols = wg == 0 && L.tile_cols >= (int64_t)kShortColsPerTile * L.n_tiles;
   const auto tiled = [&](cudaStream_t s) {
-    if (short_cols)
+    if (kind == kKernelDirect) {
+      if (direct_per_sm == 3)
+        bellman_direct_kernel<kDirectWarps, 3><<<mg, 32 * kDirectWarps, 0, s>>>(L);
+      else
+        bellman_direct_kernel<kDirectWarps, 4><<<mg, 32 * kDirectWarps, 0, s>>>(L);
+    } else if (short_cols) {
       bellman_step_kernel<kConsumersShort>
           <<<mg, 32 * (kConsumersShort + 1), sizeof(Smem<kConsumersShort>), s>>>(L);
-    else
+    } else {
       bellman_step_kernel<kConsumersLong><<<mg, 32 * (kConsumersLong + 1), sizeof(Smem<kConsumersLong>), s>>>(L);
+    }
     return cudaGetLastError();
   };
   cudaError_t e = cudaSuccess;
   if (wg > 0 && side && side->stream && L.n_tiles > 0) {
-    // fork / join: the tiled kernel is issued first so that its persistent CTAs
-    // hold the SMs; wide CTAs run in the room left beside them
+    // fork / join: the tiled kernel is issued first so that its CTAs hold the
+    // SMs; wide CTAs run in the room left beside them
     e = cudaEventRecord(side->fork, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(side->stream, side->fork, 0);
     if (e != cudaSuccess) return e;

@@ -115,6 +115,19 @@ struct StepControl {
   unsigned int finished;   // CTAs (of both step kernels) finished in the running launch
   unsigned int error;      // nonzero: a bounded wait inside the kernel gave up
   unsigned int wide_next;  // next wide state to take in the running launch
+  unsigned int tile_next;  // next tile to take in the running launch (direct kernel)
+};
+
+// Launch configuration of the Bellman step (per session; chosen by rule or by
+// the autotuner). Zero fields mean "by rule".
+enum : int32_t { kKernelRule = 0, kKernelRing = 1, kKernelDirect = 2 };
+constexpr int kDirectWarps = 8;  // warps per CTA of the direct kernel
+struct LaunchConfig {
+  int32_t kernel = kKernelRule;  // ring: TMA-fed shared-memory tiles; direct: warps stream tiles from global memory
+  int32_t cta_warps = 0;         // ring: 16 or 24 warps per CTA; direct: 8
+  int32_t ctas_per_sm = 0;       // direct: 3 or 4 CTAs per SM
+  int32_t tile_entries = 0;      // tile plan: entries per tile (<= kTileEntries)
+  int32_t wide_col = 0;          // columns this long make their state wide
 };
 
 // Second stream on which the wide-state kernel runs beside the tiled one.
@@ -167,12 +180,21 @@ extern std::atomic<int> g_stall_producer;
 // One Bellman iteration: the wide-state kernel (on `side`, beside the tiled one,
 // when given) and the tiled kernel; the last CTA of the two advances the
 // iteration state.
-cudaError_t launch_bellman_step(const StepLaunch& L, int grid, cudaStream_t st, const SideStream* side = nullptr);
+// `cfg` (nullable) picks the tiled kernel and its shape; the tile list in `L`
+// must follow the same configuration's tile plan.
+cudaError_t launch_bellman_step(const StepLaunch& L, int grid, cudaStream_t st, const SideStream* side = nullptr,
+                                const LaunchConfig* cfg = nullptr);
 // CTAs of the persistent tiled kernel: one per SM.
 int bellman_grid();
+// The configuration a launch of `L` with `cfg` (nullable) actually uses: kernel,
+// warps per CTA and CTAs per SM resolved by the rule where `cfg` leaves them open.
+LaunchConfig resolve_launch(const StepLaunch& L, const LaunchConfig* cfg);
 // Tile plan for one problem's model (host): tiles appended to `out`, wide
-// states (no tile) appended to `wide`.
-void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out, std::vector<int32_t>& wide);
+// states (no tile) appended to `wide`. Tiles hold at most `tile_entries`
+// entries (<= kTileEntries; 0: kTileEntries); a state with a column of
+// `wide_col` entries or more (0: kWideCol) is wide.
+void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out, std::vector<int32_t>& wide,
+                int32_t tile_entries = 0, int32_t wide_col = 0);
 
 // model.cu
 imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, const int32_t* stateptr,
@@ -214,6 +236,7 @@ struct Session {
   int2* wide = nullptr;
   int32_t n_wide = 0;
   SideStream side;  // created when the session has both tiles and wide states
+  LaunchConfig cfg;  // launch configuration (rule, set_launch or the autotuner)
   StepLaunch L{};
   int grid = 1;
   cudaGraphExec_t graph = nullptr;
@@ -227,6 +250,12 @@ struct Session {
   static imdp_status create(const std::vector<DevModel*>& ms, const std::vector<const imdp_spec*>& specs,
                             const int32_t* want_policy, cudaStream_t st, Session** out);
   imdp_status reset(cudaStream_t st);
+  // Upload a tile plan (tiles and wide states of every problem) and point the
+  // launch at it.
+  imdp_status install_plan(const std::vector<Tile>& tiles, const std::vector<int2>& wide, cudaStream_t st);
+  // Use launch configuration `c` from the next step on (re-plans the tiles
+  // when its plan limits differ; drops the captured graph).
+  imdp_status set_launch(const LaunchConfig& c, cudaStream_t st);
   imdp_status step(int32_t n, cudaStream_t st);
   imdp_status run(int32_t check_every, cudaStream_t st);
   imdp_status read_states(std::vector<IterState>& out, cudaStream_t st);

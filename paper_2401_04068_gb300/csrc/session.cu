@@ -167,10 +167,6 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
     for (size_t t = at; t < tiles.size(); ++t) tiles[t].p = p;
     for (int32_t s : ms[p]->h_wide) wide.push_back(make_int2(p, s));
   }
-  S->n_tiles = (int32_t)tiles.size();
-  S->tiles = S->alloc<Tile>(tiles.size());
-  S->n_wide = (int32_t)wide.size();
-  S->wide = S->alloc<int2>(wide.size());
   // each problem's hint block starts on a 16-byte boundary and is padded, so
   // the kernel's bulk copies of hint windows stay aligned and in bounds
   for (int p = 0; p < count; ++p) S->total_cols += (int64_t)padded_i32(ms[p]->n_cols);
@@ -181,7 +177,7 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   S->probs = S->alloc<Problem>(count);
   S->its = S->alloc<IterState>(count);
   S->ctl = S->alloc<StepControl>(1);
-  if (!S->hints || !S->wide || !S->tiles || !S->fixed || !S->V || !S->base || !S->probs || !S->its || !S->ctl) {
+  if (!S->hints || !S->fixed || !S->V || !S->base || !S->probs || !S->its || !S->ctl) {
     delete S; set_error("device allocation failed (session)"); return IMDP_ENOMEM;
   }
   S->probs_h.resize(count);
@@ -253,10 +249,6 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   if (e == cudaSuccess) e = cudaMemcpyAsync(S->fixed, fixed.data(), total, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S->base, S->base_h.data(), sizeof(int32_t) * (count + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S->probs, S->probs_h.data(), sizeof(Problem) * count, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && !tiles.empty())
-    e = cudaMemcpyAsync(S->tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && !wide.empty())
-    e = cudaMemcpyAsync(S->wide, wide.data(), sizeof(int2) * wide.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host staging vectors go out of scope
   if (e != cudaSuccess) { delete S; return cuda_status(e, "session setup"); }
   S->L.probs = S->probs;
@@ -266,20 +258,70 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   S->L.count = count;
   S->L.total_states = (int32_t)total;
   S->L.any_infinite = S->any_infinite ? 1 : 0;
-  S->L.tiles = S->tiles;
-  S->L.n_tiles = S->n_tiles;
-  S->L.tile_cols = 0;
-  for (int p = 0; p < count; ++p) S->L.tile_cols += ms[p]->tile_cols;
-  S->L.wide = S->wide;
-  S->L.n_wide = S->n_wide;
-  if (S->n_wide > 0 && S->n_tiles > 0 && (e = S->side.create()) != cudaSuccess) {
-    delete S;
-    return cuda_status(e, "session side stream");
-  }
   S->grid = bellman_grid();
-  imdp_status r = S->reset(st);
+  imdp_status r = S->install_plan(tiles, wide, st);
+  if (r != IMDP_OK) { delete S; return r; }
+  r = S->reset(st);
   if (r != IMDP_OK) { delete S; return r; }
   *out = S;
+  return IMDP_OK;
+}
+
+imdp_status Session::install_plan(const std::vector<Tile>& tl, const std::vector<int2>& wl, cudaStream_t st) {
+  auto release = [&](void* p) {
+    if (!p) return;
+    allocs.erase(std::remove(allocs.begin(), allocs.end(), p), allocs.end());
+    cudaFree(p);
+  };
+  cudaError_t e = cudaStreamSynchronize(st);  // launches in flight may still read the old plan
+  if (e != cudaSuccess) return cuda_status(e, "session plan");
+  release(tiles);
+  release(wide);
+  tiles = alloc<Tile>(tl.size());
+  wide = alloc<int2>(wl.size());
+  if (!tiles || !wide) { set_error("device allocation failed (tile plan)"); return IMDP_ENOMEM; }
+  if (!tl.empty()) e = cudaMemcpyAsync(tiles, tl.data(), sizeof(Tile) * tl.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !wl.empty())
+    e = cudaMemcpyAsync(wide, wl.data(), sizeof(int2) * wl.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors belong to the caller
+  if (e != cudaSuccess) return cuda_status(e, "session plan");
+  n_tiles = (int32_t)tl.size();
+  n_wide = (int32_t)wl.size();
+  L.tiles = tiles;
+  L.n_tiles = n_tiles;
+  L.wide = wide;
+  L.n_wide = n_wide;
+  L.tile_cols = 0;
+  for (const Tile& T : tl) L.tile_cols += T.c1 - T.c0;
+  if (n_wide > 0 && n_tiles > 0 && !side.stream && (e = side.create()) != cudaSuccess)
+    return cuda_status(e, "session side stream");
+  if (graph) {
+    cudaGraphExecDestroy(graph);
+    graph = nullptr;
+  }
+  return IMDP_OK;
+}
+
+imdp_status Session::set_launch(const LaunchConfig& c, cudaStream_t st) {
+  const LaunchConfig old = resolve_launch(L, &cfg), now = resolve_launch(L, &c);
+  if (now.tile_entries != old.tile_entries || now.wide_col != old.wide_col) {
+    std::vector<Tile> tl;
+    std::vector<int2> wl;
+    for (int p = 0; p < count; ++p) {
+      std::vector<int32_t> ws;
+      const size_t at = tl.size();
+      plan_tiles(models[p], p, tl, ws, now.tile_entries, now.wide_col);
+      for (size_t t = at; t < tl.size(); ++t) tl[t].p = p;
+      for (int32_t s : ws) wl.push_back(make_int2(p, s));
+    }
+    imdp_status r = install_plan(tl, wl, st);
+    if (r != IMDP_OK) return r;
+  }
+  cfg = c;
+  if (graph) {
+    cudaGraphExecDestroy(graph);
+    graph = nullptr;
+  }
   return IMDP_OK;
 }
 
@@ -321,7 +363,7 @@ imdp_status Session::step(int32_t n, cudaStream_t st) {
       cudaGraph_t g = nullptr;
       graph_stalled = g_stall_producer.load() != 0;
       e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-      for (int i = 0; i < kGraphChunk && e == cudaSuccess; ++i) e = launch_bellman_step(L, grid, st, &side);
+      for (int i = 0; i < kGraphChunk && e == cudaSuccess; ++i) e = launch_bellman_step(L, grid, st, &side, &cfg);
       cudaError_t e2 = cudaStreamEndCapture(st, &g);
       if (e == cudaSuccess) e = e2;
       if (e == cudaSuccess) e = cudaGraphInstantiate(&graph, g, 0);
@@ -333,7 +375,7 @@ imdp_status Session::step(int32_t n, cudaStream_t st) {
     }
     for (; done + kGraphChunk <= n && e == cudaSuccess; done += kGraphChunk) e = cudaGraphLaunch(graph, st);
   }
-  for (; done < n && e == cudaSuccess; ++done) e = launch_bellman_step(L, grid, st, &side);
+  for (; done < n && e == cudaSuccess; ++done) e = launch_bellman_step(L, grid, st, &side, &cfg);
   if (e != cudaSuccess) return cuda_status(e, "bellman step");
   launches += n;
   launched_since_reset += n;

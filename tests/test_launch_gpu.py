@@ -1,0 +1,125 @@
+"""Launch configurations of the Bellman step and the autotuner, through the C ABI.
+
+Every configuration (ring or direct kernel, warps per CTA, CTAs per SM, tile
+size, wide-state threshold) must compute the same words: each column's value
+is the same multiset of exact integer terms whichever kernel runs it. Checked
+bitwise between configurations and against the oracle within TOL_F64."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import paper_2401_04068_gb300 as g
+from gpu_helpers import TOL_F64, run_oracle
+from workloads import banded_batch, banded_imdp
+
+pytestmark = pytest.mark.gpu
+
+CONFIGS = [
+    dict(kernel=g.KERNEL_RING, cta_warps=16),
+    dict(kernel=g.KERNEL_RING, cta_warps=24),
+    dict(kernel=g.KERNEL_DIRECT, ctas_per_sm=4),
+    dict(kernel=g.KERNEL_DIRECT, ctas_per_sm=3),
+    dict(kernel=g.KERNEL_DIRECT, ctas_per_sm=4, tile_entries=300),
+    dict(kernel=g.KERNEL_RING, cta_warps=16, tile_entries=700, wide_col=200),
+    dict(kernel=g.KERNEL_DIRECT, ctas_per_sm=4, wide_col=1 << 30),
+    dict(kernel=g.KERNEL_DIRECT, ctas_per_sm=3, wide_col=150),
+]
+
+
+def _run(model, m, spec, cfg, steps):
+    sess = g.imdp_session_create([model], [spec])
+    g.imdp_session_set_launch(sess, **cfg)
+    g.imdp_session_step(sess, steps)
+    raw, k = g.imdp_session_checkpoint(sess, 0)
+    V = np.zeros(m.n_states)
+    g.imdp_session_read(sess, 0, V, check=False)
+    resolved = g.imdp_session_get_launch(sess)
+    sess.close()
+    return raw, k, V, resolved
+
+
+@pytest.mark.parametrize("case", ["reach", "reach_avoid_opt", "reward", "infinite", "f32", "mixed_wide"])
+def test_every_launch_config_gives_the_same_words(case):
+    if case == "mixed_wide":
+        # short, medium and long columns in one model: tiles and wide states
+        m = banded_imdp(900, 2, 900 * 2 * 180 + 900 * 2 + 1, eps=0.1, seed=61)
+    else:
+        m = banded_imdp(700, 3, 700 * 3 * 40 + 700 * 3 + 1, eps=0.1, seed=60)
+    model = g.create_model(m, dtype=g.IMDP_F32 if case == "f32" else g.IMDP_F64)
+    K = 40
+    okw = dict(horizon=K, reach=m.goal)
+    if case == "reach_avoid_opt":
+        avoid = np.setdiff1d(np.arange(0, m.n_states, 29), m.goal)
+        okw.update(property=g.IMDP_REACH_AVOID, avoid=avoid, pessimistic=False, maximize=False)
+    elif case == "reward":
+        r = np.random.default_rng(2).uniform(-1, 2, m.n_states)
+        okw = dict(property=g.IMDP_REWARD, horizon=K, reward=r, discount=0.9)
+    elif case == "infinite":
+        okw = dict(infinite_time=True, eps=1e-8, horizon=5000, reach=m.goal)
+    spec = g.make_spec(**okw)
+    steps = 5000 if case == "infinite" else K
+    ref = None
+    for cfg in CONFIGS:
+        raw, k, V, resolved = _run(model, m, spec, cfg, steps)
+        assert resolved["kernel"] == cfg["kernel"]
+        if ref is None:
+            ref = (raw, k, V)
+            ost, oV, ok, _, _ = run_oracle(m, **okw)
+            # the stopping test compares the residual in each side's arithmetic;
+            # at the threshold the two may stop one iteration apart
+            assert abs(k - ok) <= (1 if case == "infinite" else 0)
+            tol = TOL_F64 * max(1.0, float(np.max(np.abs(oV))))
+            if case == "f32":
+                tol = K * model.error_bound() + TOL_F64
+            if case == "infinite":
+                tol = 1e-7
+            assert float(np.max(np.abs(V - oV))) <= tol
+        else:
+            assert k == ref[1], cfg
+            assert np.array_equal(raw, ref[0]), cfg
+    model.close()
+
+
+def test_heterogeneous_batch_direct_equals_ring():
+    ms = [banded_imdp(150 + 40 * i, 1 + i % 3, (150 + 40 * i) * (1 + i % 3) * (8 + 7 * i) + 1, seed=80 + i)
+          for i in range(6)]
+    models = [g.create_model(x) for x in ms]
+    specs = [g.make_spec(horizon=10 + 5 * i, reach=x.goal, pessimistic=i % 2 == 0) for i, x in enumerate(ms)]
+    outs = {}
+    for cfg in (dict(kernel=g.KERNEL_RING), dict(kernel=g.KERNEL_DIRECT, ctas_per_sm=4, tile_entries=256)):
+        sess = g.imdp_session_create(models, specs)
+        g.imdp_session_set_launch(sess, **cfg)
+        g.imdp_session_run(sess)
+        outs[cfg["kernel"]] = [g.imdp_session_checkpoint(sess, i) for i in range(len(ms))]
+        sess.close()
+    for (ra, ka), (rb, kb) in zip(outs[g.KERNEL_RING], outs[g.KERNEL_DIRECT]):
+        assert ka == kb and np.array_equal(ra, rb)
+
+
+def test_autotune_picks_a_config_and_caches_it(tmp_path):
+    m = banded_batch(64, 120, 1, 120 * 30 + 120 + 1, eps=0.05, seed=7)
+    model = g.create_model(m)
+    spec = g.make_spec(horizon=30, reach=m.goal)
+    cache = str(tmp_path / "tuned.json")
+    sess = g.imdp_session_create([model], [spec])
+    cfg, ms = g.imdp_session_autotune(sess, 8, cache)
+    assert ms > 0 and cfg["kernel"] in (g.KERNEL_RING, g.KERNEL_DIRECT)
+    data = json.load(open(cache))
+    assert len(data) == 1
+    entry = next(iter(data.values()))
+    assert entry["kernel"] == cfg["kernel"] and entry["ms_per_iter"] > 0
+    # the tuned session still answers the query exactly
+    g.imdp_session_run(sess)
+    V = np.zeros(m.n_states)
+    g.imdp_session_read(sess, 0, V)
+    _, oV, _, _, _ = run_oracle(m, horizon=30, reach=m.goal)
+    np.testing.assert_allclose(V, oV, rtol=0, atol=TOL_F64)
+    sess.close()
+    # a second session of the same shape takes the cached choice without timing
+    sess2 = g.imdp_session_create([model], [spec])
+    cfg2, ms2 = g.imdp_session_autotune(sess2, 8, cache)
+    assert ms2 == 0.0 and cfg2 == cfg
+    sess2.close()
+    assert os.path.exists(cache)
