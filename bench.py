@@ -255,6 +255,7 @@ def run_ours(args, rank, world, local_rank):
     else:
         spec = g.make_spec(horizon=args.horizon, reach=m.goal, pessimistic=True, maximize=True)
     sess = g.imdp_session_create([model], [spec], want_policy=[1] if args.policy else None, stream=stream)
+    launch = apply_launch(g, sess, args, stream, min(args.horizon, 64) if not args.infinite else 64)
 
     def one_step(ev=None):
         g.imdp_session_reset(sess, stream)
@@ -336,9 +337,10 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_peak_hbm()
     alg_bytes = algorithmic_bytes_per_iteration(m, args.dtype)
     launch_ms = kernel_ms / max(1, launches)  # per launched iteration (includes any past convergence)
-    n_tiles, n_wide, wide_entries = g.imdp_model_plan(model)
+    n_tiles, n_wide, wide_entries = g.imdp_session_plan(sess)
     wide_share = wide_entries / max(1, m.nnz)
-    kernel = "bellman_wide_kernel" if wide_share > 0.5 else "bellman_step_kernel"
+    kernel = "bellman_wide_kernel" if wide_share > 0.5 else \
+        ("bellman_direct_kernel" if launch["kernel"] == 2 else "bellman_step_kernel")
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
     traffic = recorded_traffic(args.workload + ("" if args.dtype == "f64" else ":f32"))
     cfg = workload_config(args.workload, m, args.horizon)
@@ -354,6 +356,7 @@ def run_ours(args, rank, world, local_rank):
         cfg["policy"] = "time-dependent, K x n int32 written every iteration"
     cfg["storage"] = "32-bit bounds (per-column scaled), 64-bit arithmetic" if args.dtype == "f32" else \
         "64-bit bounds (Q1.63), 64-bit arithmetic"
+    cfg["launch"] = launch
     if args.dtype == "f32":
         cfg["error_bound_per_iteration"] = model.error_bound()
         cfg["error_bound_horizon"] = model.error_bound() * args.horizon
@@ -370,8 +373,7 @@ def run_ours(args, rank, world, local_rank):
                      "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": launch_ms,
                      "plan": {"tiles": n_tiles, "wide_states": n_wide, "wide_entry_share": wide_share,
-                              # the launcher's rule: 24-warp CTAs for >= 16 columns per tile, no wide states
-                              "tiled_cta_warps": 24 if (n_wide == 0 and len(m.colptr) - 1 >= 16 * n_tiles) else 16},
+                              "launch": launch},
                      "timing": "CUDA events around each step's launches (both step kernels) / launches"},
         "clocks": clk,
         # step kernels (two per iteration when the model has wide states) + one value-reset kernel per step
@@ -381,6 +383,42 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(m, iters, budget_s=args.ref_budget)  # same per-iteration work
     print(json.dumps(out), flush=True)
+
+
+TUNE_CACHE = os.path.join(ROOT, "paper_2401_04068_gb300", "tuned_gb300.json")
+
+
+def parse_launch(text: str) -> dict:
+    """'ring[:warps]' or 'direct[:ctas_per_sm[:tile_entries[:wide_col]]]' -> launch fields."""
+    parts = text.split(":")
+    kind = {"ring": 1, "direct": 2}[parts[0]]
+    nums = [int(x) for x in parts[1:]]
+    if kind == 1:
+        keys = ["cta_warps", "tile_entries", "wide_col"]
+    else:
+        keys = ["ctas_per_sm", "tile_entries", "wide_col"]
+    out = {"kernel": kind}
+    out.update(dict(zip(keys, nums)))
+    return out
+
+
+def apply_launch(g, sess, args, stream, tune_iters: int) -> dict:
+    """Launch configuration of the timed session: explicit (--launch), the
+    autotuner's cached or freshly timed choice (--tune), or the rule."""
+    if args.launch:
+        g.imdp_session_set_launch(sess, stream=stream, **parse_launch(args.launch))
+        how = "explicit"
+    elif args.tune != "off":
+        cache = args.tune_cache or TUNE_CACHE
+        if args.tune == "fresh":
+            cache = None
+        _, ms = g.imdp_session_autotune(sess, tune_iters, cache, stream=stream)
+        how = "autotuner (cached choice)" if ms == 0.0 else f"autotuner (timed now: {ms:.4f} ms per iteration)"
+    else:
+        how = "rule"
+    out = g.imdp_session_get_launch(sess)
+    out["chosen_by"] = how
+    return out
 
 
 def _gpu_setup(rank, world, local_rank):
@@ -414,6 +452,7 @@ def run_uneven(args, rank, world, local_rank):
     specs = [g.make_spec(horizon=int(K), reach=m.goal, pessimistic=True, maximize=True) for m, K in zip(ms, Ks)]
     sess = g.imdp_session_create(models, specs, stream=stream)
     kmax = int(Ks.max())
+    launch = apply_launch(g, sess, args, stream, 64)
 
     def one_step(ev=None):
         g.imdp_session_reset(sess, stream)
@@ -467,11 +506,107 @@ def run_uneven(args, rank, world, local_rank):
                    "states": int(sum(m.n_states for m in ms)), "horizon": "U{50..500} per problem",
                    "max_horizon": kmax, "shapes": "states U{6..961}, actions U{1..4}, window U{2..min(400,n)}",
                    "l2": "inputs larger than L2 (%.1f GB resident)" % (nnz.sum() * 20 / 1e9),
-                   "generation_s": round(gen_s, 1), "parallelism": "replicas"},
+                   "generation_s": round(gen_s, 1), "parallelism": "replicas", "launch": launch},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_kind": peak_kind, "kernel": "bellman_step_kernel",
+                     "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "bellman_direct_kernel" if launch["kernel"] == 2 else "bellman_step_kernel",
                      "note": "algorithmic bytes of every running problem summed over the step's launches"},
         "clocks": clk, "gpu_launches": int(launches + args.steps), "e2e": None,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_latency(args, rank, world, local_rank):
+    """Single small model (the Sec. 3.1 worked example, K = 100, or the linear_5
+    shape, K = 200): latency of one query. Three views: the public call
+    imdp_value_iteration with a host output buffer (session set-up, launches and
+    read-back inside), a resident session (reset + K launches + read to the host),
+    and the device time of the K launches alone (CUDA events)."""
+    import torch
+    import paper_2401_04068_gb300 as g
+    from workloads import make_config
+    dev = _gpu_setup(rank, world, local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    if args.workload == "worked_example":
+        ex = json.load(open(os.path.join(ROOT, "tests", "golden", "worked_example.json")))
+
+        class _M:
+            pass
+        m = _M()
+        m.n_states = ex["n_states"]
+        for k in ("stateptr", "colptr", "rowval"):
+            setattr(m, k, np.asarray(ex[k], np.int32))
+        m.lower = np.asarray(ex["lower"], np.float64)
+        m.upper = np.asarray(ex["upper"], np.float64)
+        m.goal = np.asarray(ex["goal"], np.int32)
+        K = 100
+    else:
+        m = make_config("linear5")
+        K = 200
+    nnz, ncols = len(m.rowval), len(m.colptr) - 1
+    model = g.create_model(m, stream=stream)
+    spec = g.make_spec(horizon=K, reach=m.goal)
+    Vh = torch.empty(m.n_states, dtype=torch.float64).pin_memory()
+    kk = [0]
+    n = max(args.steps, 20)
+
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            out.append((time.perf_counter() - t) * 1e3)
+        return out
+
+    for _ in range(max(args.warmup, 3)):
+        g.imdp_value_iteration(model, spec, Vh, kk, stream=stream)
+    e2e = timed(lambda: g.imdp_value_iteration(model, spec, Vh, kk, stream=stream), n)
+    assert kk[0] == K
+    sess = g.imdp_session_create([model], [spec], stream=stream)
+
+    def resident():
+        g.imdp_session_reset(sess, stream)
+        g.imdp_session_step(sess, K, stream)
+        g.imdp_session_read(sess, 0, Vh, kk, stream=stream)
+
+    for _ in range(3):
+        resident()
+    res = timed(resident, n)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    for a, b in ev:
+        g.imdp_session_reset(sess, stream)
+        a.record(stream)
+        g.imdp_session_step(sess, K, stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    dev_ms = [a.elapsed_time(b) for a, b in ev]
+    pct = lambda xs, q: float(np.percentile(np.asarray(xs), q))
+    if rank != 0:
+        return
+    out = {
+        "metric": "query latency, one small model (K Bellman iterations per query)", "value": pct(e2e, 50),
+        "unit": "ms per query", "n_gpus": world, "steps": n, "warmup": max(args.warmup, 3),
+        "ms_per_step": pct(e2e, 50), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "the paper's worked example (Sec. 3.1)" if args.workload == "worked_example"
+        else "synthetic (seeded banded IMDP shaped like linear_5_states)",
+        "config": {"workload": args.workload, "states": int(m.n_states), "columns": ncols, "transitions": nnz,
+                   "horizon": K, "query": "maximize pessimistic reachability, finite horizon",
+                   "parallelism": "replicas", "l2": "model resident in L2 (a few hundred bytes)"},
+        "latency_ms": {
+            "value_iteration_call": {"p50": pct(e2e, 50), "p99": pct(e2e, 99)},
+            "resident_session_reset_step_read": {"p50": pct(res, 50), "p99": pct(res, 99)},
+            "device_K_launches": {"p50": pct(dev_ms, 50), "p99": pct(dev_ms, 99),
+                                  "us_per_iteration": pct(dev_ms, 50) * 1e3 / K},
+        },
+        "transition_updates_per_s": nnz * K / (pct(e2e, 50) / 1e3),
+        "clocks": clk, "gpu_launches": int(K * n), "roofline": None,
+        "e2e": {"value": pct(e2e, 50), "unit": "ms per query", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(m.n_states * 8)},
     }
     print(json.dumps(out), flush=True)
 
@@ -667,6 +802,10 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="storage of the transition bounds")
+    ap.add_argument("--launch", default="", help="explicit launch configuration, e.g. ring:24 or direct:4:1024")
+    ap.add_argument("--tune", default="cache", choices=["cache", "fresh", "off"],
+                    help="autotuner: cached choice (timing only shapes missing from the cache), time now, or rule")
+    ap.add_argument("--tune-cache", default="", help="autotuner cache file (default: the package's GB300 table)")
     ap.add_argument("--requests", type=int, default=2000, help="served workload: number of requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="served workload: Poisson arrival rate per second")
     ap.add_argument("--server-budget-gb", type=float, default=16.0, help="served workload: HBM budget of the server")
@@ -690,6 +829,8 @@ def main():
     try:
         if args.workload.startswith("uneven"):
             run_uneven(args, rank, world, local_rank)
+        elif args.workload in ("worked_example", "linear5"):
+            run_latency(args, rank, world, local_rank)
         elif args.workload.startswith("served"):
             run_served(args, rank, world, local_rank)
         elif args.shard == "states":

@@ -65,9 +65,14 @@ typedef enum {
 /* Storage precision of the transition bounds. IMDP_F64 keeps 64 bits per bound
  * (stored as unsigned fixed point with 63 fractional bits, which resolves
  * probabilities in [0, 1] to 1.1e-19 absolute, finer than binary64 near 1).
- * IMDP_F32 keeps 32 bits per bound: per column, mantissas scaled to the column's
- * largest upper bound (resolution ~2^-31 of it), 12 bytes per transition instead
- * of 20; arithmetic stays 64-bit. See imdp_model_error_bound. */
+ * IMDP_F32 is the fast path: 32 bits per bound (per column, mantissas scaled to
+ * the column's largest upper bound, resolution ~2^-31 of it), 12 bytes per
+ * transition instead of 20, values kept at 32 bits and 32-bit arithmetic in the
+ * hot loop, with a correction stage: a column whose rounding would move a
+ * Bellman step by more than a per-iteration budget (default 5e-9, i.e. 1e-6
+ * over K = 200 iterations; see imdp_create_csc_f32) keeps its exact 64-bit
+ * bounds and runs the 64-bit routines. imdp_model_error_bound gives the
+ * resulting guaranteed bound. */
 typedef enum { IMDP_F64 = 0, IMDP_F32 = 1 } imdp_dtype;
 
 /* Property types of the specification JSON schema (Appendix A). */
@@ -127,6 +132,23 @@ IMDP_API imdp_status imdp_create_csc(int32_t n_states, int32_t n_cols, int64_t n
                             const double* upper, imdp_dtype dtype, void* stream, imdp_model** out);
 
 /*
+ * imdp_create_csc with IMDP_F32 storage and a chosen per-iteration error budget
+ * (no counterpart in the paper, which computes in binary64 only). Every column
+ * whose 32-bit rounding error, sum |dlower| + |dupper|, plus 2^-32 for the
+ * rounding of the values, exceeds `budget_per_iteration` is a correction column
+ * and keeps its exact bounds (20 bytes per transition instead of 12).
+ * budget 0 keeps every column exact; a large budget (e.g. 1) none. IMDP_EINVAL
+ * for a negative or NaN budget; other arguments and errors as imdp_create_csc.
+ */
+IMDP_API imdp_status imdp_create_csc_f32(int32_t n_states, int32_t n_cols, int64_t nnz, const int32_t* stateptr,
+                                         const int32_t* colptr, const int32_t* rowval, const double* lower,
+                                         const double* upper, double budget_per_iteration, void* stream,
+                                         imdp_model** out);
+/* Correction columns of an IMDP_F32 model: how many, their transitions, and the
+ * budget they were chosen by (all 0 for IMDP_F64). Any output may be NULL. */
+IMDP_API imdp_status imdp_model_exact_columns(const imdp_model* m, int32_t* n_exact, int64_t* exact_entries,
+                                              double* budget_per_iteration);
+/*
  * Create a model from dense bounds (Sec. 3.1: IntervalProbabilities with rows =
  * destination states and columns = actions, concatenated over source states).
  *   n_actions      int32[n_states]: number of actions of each state (>= 1)
@@ -146,11 +168,14 @@ IMDP_API imdp_status imdp_model_info(const imdp_model* m, int32_t* n_states, int
                             size_t* device_bytes, int32_t* max_col_nnz);
 
 /*
- * A-priori error bound of the model's storage: for IMDP_F32, the largest sum over
- * one column of |lower - stored lower| + |upper - stored upper|. Values lie in
- * [0, 1] and the Bellman operator is non-expansive, so K iterations of a
- * reachability problem on the stored model stay within K * bound of the
- * binary64 answer (scale by the reward range for rewards). 0 for IMDP_F64.
+ * Guaranteed per-iteration error bound of IMDP_F32 storage: the largest sum over
+ * one 32-bit column of |lower - stored lower| + |upper - stored upper| (how far
+ * the stored intervals move one column's optimum), plus 2^-32 (values kept at
+ * 32 bits, rounded to nearest), plus (k_max + 1) 2^-62 (truncated products).
+ * Correction columns contribute no rounding. Values lie in [0, 1] and the
+ * Bellman operator is non-expansive, so K iterations of a reachability problem
+ * stay within K * bound of exact value iteration on the given intervals (scale
+ * by the reward map's range for rewards). 0 for IMDP_F64.
  */
 IMDP_API imdp_status imdp_model_error_bound(const imdp_model* m, double* per_iteration);
 
@@ -287,6 +312,11 @@ IMDP_API imdp_status imdp_session_set_launch(imdp_session* s, const imdp_launch_
 /* The configuration the session's launches use, with every field resolved by
  * the rule where the set configuration left it open. */
 IMDP_API imdp_status imdp_session_get_launch(const imdp_session* s, imdp_launch_config* cfg);
+/* The session's current tile plan (it follows the launch configuration's
+ * tile_entries and wide_col): tiles streamed by the tiled kernels, wide states
+ * and their transitions. Any output may be NULL. */
+IMDP_API imdp_status imdp_session_plan(const imdp_session* s, int32_t* n_tiles, int32_t* n_wide,
+                                       int64_t* wide_entries);
 /*
  * Autotuner. Times candidate launch configurations on this session (each: a
  * reset, then `iters` Bellman iterations, timed with CUDA events on `stream`
@@ -307,8 +337,12 @@ IMDP_API imdp_status imdp_session_autotune(imdp_session* s, int32_t iters, const
  * the whole model does, given all of V_{k-1}. The caller runs one session per
  * slice, steps every session one iteration at a time, and after each step
  * copies every slice's owned values into all other slices (an all-gather),
- * using imdp_session_values_get / _put on device buffers. Finite horizons only
- * (each slice would test convergence on its own states).
+ * using imdp_session_values_get / _put on device buffers. An infinite horizon
+ * on a slice never stops by itself (its own residual covers its states only):
+ * after each step the caller takes imdp_session_residual of every slice, the
+ * maximum over the slices (an all-reduce), and stops when it is below the
+ * threshold imdp_session_stop_threshold gives, which is the unsharded run's
+ * own test (imdp_session_run refuses such a session, IMDP_EINVAL).
  */
 
 /* Contiguous state ranges of about equal work (20 B per transition, 12 B per
@@ -339,6 +373,16 @@ IMDP_API imdp_status imdp_session_values_get(imdp_session* s, int32_t index, int
                                              uint64_t* dst, void* stream);
 IMDP_API imdp_status imdp_session_values_put(imdp_session* s, int32_t index, int32_t k, int32_t s0, int32_t s1,
                                              const uint64_t* src, void* stream);
+/* max over states [s0, s1) of |V_k - V_{k-1}| as a raw word (the units of the
+ * values words), written to one uint64 of DEVICE memory `dst`, asynchronously on
+ * `stream` (Eq. 2's Bellman residual, the quantity the stopping test of an
+ * infinite horizon compares). IMDP_EINVAL for k < 1, a bad range or host dst. */
+IMDP_API imdp_status imdp_session_residual(imdp_session* s, int32_t index, int32_t k, int32_t s0, int32_t s1,
+                                           uint64_t* dst, void* stream);
+/* The raw threshold of problem `index`'s stopping test: the run stops after the
+ * first iteration whose residual (raw words) is below *eps_raw. IMDP_EINVAL for
+ * a finite horizon. */
+IMDP_API imdp_status imdp_session_stop_threshold(const imdp_session* s, int32_t index, uint64_t* eps_raw);
 
 /*
  * Checkpoint and resume (not in the paper: value iteration's whole state for one

@@ -33,7 +33,8 @@ EXPORTED = [
     "imdp_session_values_put", "imdp_model_plan", "imdp_debug_stall_producer",
     "imdp_read_bmdp_tool", "imdp_write_bmdp_tool", "imdp_read_prism", "imdp_write_prism", "imdp_file_free",
     "imdp_session_checkpoint", "imdp_session_restore",
-    "imdp_session_set_launch", "imdp_session_get_launch", "imdp_session_autotune",
+    "imdp_session_set_launch", "imdp_session_get_launch", "imdp_session_autotune", "imdp_session_plan",
+    "imdp_create_csc_f32", "imdp_model_exact_columns", "imdp_session_residual", "imdp_session_stop_threshold",
 ]
 
 
@@ -116,6 +117,9 @@ def load(path: Optional[str] = None):
     lib.imdp_create_csc.argtypes = [C.c_int32, C.c_int32, C.c_int64, vp, vp, vp, vp, vp, C.c_int, vp,
                                     C.POINTER(vp)]
     lib.imdp_create_dense.argtypes = [C.c_int32, vp, vp, vp, C.c_int, vp, C.POINTER(vp)]
+    lib.imdp_create_csc_f32.argtypes = [C.c_int32, C.c_int32, C.c_int64, vp, vp, vp, vp, vp, C.c_double, vp,
+                                        C.POINTER(vp)]
+    lib.imdp_model_exact_columns.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_double)]
     lib.imdp_model_destroy.argtypes = [vp]
     lib.imdp_model_destroy.restype = None
     lib.imdp_model_info.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
@@ -126,6 +130,9 @@ def load(path: Optional[str] = None):
     lib.imdp_session_create.argtypes = [C.POINTER(vp), C.POINTER(imdp_spec), C.c_int32, vp, vp, C.POINTER(vp)]
     lib.imdp_session_set_launch.argtypes = [vp, C.POINTER(imdp_launch_config), vp]
     lib.imdp_session_get_launch.argtypes = [vp, C.POINTER(imdp_launch_config)]
+    lib.imdp_session_plan.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
+    lib.imdp_session_residual.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, vp]
+    lib.imdp_session_stop_threshold.argtypes = [vp, C.c_int32, C.POINTER(C.c_uint64)]
     lib.imdp_session_autotune.argtypes = [vp, C.c_int32, C.c_char_p, vp, C.POINTER(imdp_launch_config),
                                           C.POINTER(C.c_double)]
     lib.imdp_session_reset.argtypes = [vp, vp]
@@ -261,6 +268,25 @@ def imdp_create_csc(n_states, n_cols, nnz, stateptr, colptr, rowval, lower, uppe
                                 _ptr(lower), _ptr(upper), int(dtype), _stream(stream), C.byref(out))
     _check(st, "imdp_create_csc")
     return Model(out.value)
+
+
+def imdp_create_csc_f32(n_states, n_cols, nnz, stateptr, colptr, rowval, lower, upper, budget_per_iteration,
+                        stream=None) -> Model:
+    """32-bit storage with correction columns chosen by a per-iteration error budget."""
+    out = C.c_void_p()
+    st = load().imdp_create_csc_f32(int(n_states), int(n_cols), int(nnz), _ptr(stateptr), _ptr(colptr),
+                                    _ptr(rowval), _ptr(lower), _ptr(upper), float(budget_per_iteration),
+                                    _stream(stream), C.byref(out))
+    _check(st, "imdp_create_csc_f32")
+    return Model(out.value)
+
+
+def imdp_model_exact_columns(model: Model):
+    """(correction columns, their transitions, the budget they were chosen by) of an IMDP_F32 model."""
+    n, e, b = C.c_int32(0), C.c_int64(0), C.c_double(0.0)
+    _check(load().imdp_model_exact_columns(C.c_void_p(model.handle), C.byref(n), C.byref(e), C.byref(b)),
+           "imdp_model_exact_columns")
+    return n.value, e.value, b.value
 
 
 def imdp_create_dense(n_states, n_actions, lower, upper, dtype=IMDP_F64, stream=None) -> Model:
@@ -403,6 +429,27 @@ def imdp_session_get_launch(s: Session) -> dict:
     return cfg.as_dict()
 
 
+def imdp_session_residual(s: Session, index: int, k: int, s0: int, s1: int, dst, stream=None):
+    """max |V_k - V_{k-1}| over states [s0, s1) (raw word) into one device word ``dst``."""
+    _check(load().imdp_session_residual(C.c_void_p(s.handle), int(index), int(k), int(s0), int(s1), _ptr(dst),
+                                        _stream(stream)), "imdp_session_residual")
+
+
+def imdp_session_stop_threshold(s: Session, index: int) -> int:
+    """Raw threshold of the infinite-horizon stopping test of problem ``index``."""
+    e = C.c_uint64(0)
+    _check(load().imdp_session_stop_threshold(C.c_void_p(s.handle), int(index), C.byref(e)),
+           "imdp_session_stop_threshold")
+    return int(e.value)
+
+
+def imdp_session_plan(s: Session):
+    """(tiles, wide states, transitions of wide states) of the session's current tile plan."""
+    t, w, e = C.c_int32(0), C.c_int32(0), C.c_int64(0)
+    _check(load().imdp_session_plan(C.c_void_p(s.handle), C.byref(t), C.byref(w), C.byref(e)), "imdp_session_plan")
+    return t.value, w.value, e.value
+
+
 def imdp_session_autotune(s: Session, iters: int, cache_path: Optional[str] = None, stream=None):
     """Time the candidate launch configurations (or take the cached choice) and
     keep the fastest. Returns (configuration dict, ms per iteration; 0 when cached)."""
@@ -494,12 +541,17 @@ def imdp_server_destroy(server: Server):
 
 # ---------------------------------------------------------------- convenience wrappers (host numpy in/out)
 
-def create_model(m, dtype=IMDP_F64, stream=None) -> Model:
-    """Model from any object with n_states/stateptr/colptr/rowval/lower/upper."""
-    return imdp_create_csc(m.n_states, len(m.colptr) - 1, len(m.rowval), np.ascontiguousarray(m.stateptr, np.int32),
-                           np.ascontiguousarray(m.colptr, np.int32), np.ascontiguousarray(m.rowval, np.int32),
-                           np.ascontiguousarray(m.lower, np.float64), np.ascontiguousarray(m.upper, np.float64),
-                           dtype, stream)
+def create_model(m, dtype=IMDP_F64, stream=None, budget=None) -> Model:
+    """Model from any object with n_states/stateptr/colptr/rowval/lower/upper.
+    ``budget``: per-iteration error budget of 32-bit storage (IMDP_F32 only)."""
+    arrs = (np.ascontiguousarray(m.stateptr, np.int32), np.ascontiguousarray(m.colptr, np.int32),
+            np.ascontiguousarray(m.rowval, np.int32), np.ascontiguousarray(m.lower, np.float64),
+            np.ascontiguousarray(m.upper, np.float64))
+    if budget is not None:
+        if dtype != IMDP_F32:
+            raise ValueError("a budget applies to IMDP_F32 storage only")
+        return imdp_create_csc_f32(m.n_states, len(m.colptr) - 1, len(m.rowval), *arrs, budget, stream)
+    return imdp_create_csc(m.n_states, len(m.colptr) - 1, len(m.rowval), *arrs, dtype, stream)
 
 
 def value_iteration(model: Model, n_states: int, policy: bool = False, stream=None, **spec_kw):

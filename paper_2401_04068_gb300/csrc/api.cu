@@ -137,6 +137,32 @@ void imdp_model_destroy(imdp_model* m) {
   delete m;
 }
 
+imdp_status imdp_create_csc_f32(int32_t n_states, int32_t n_cols, int64_t nnz, const int32_t* stateptr,
+                                const int32_t* colptr, const int32_t* rowval, const double* lower,
+                                const double* upper, double budget_per_iteration, void* stream, imdp_model** out) {
+  set_error("");
+  if (!have_device()) { set_error("no CUDA device"); return IMDP_EDEVICE; }
+  DevModel* m = nullptr;
+  imdp_status s = model_create_csc(n_states, n_cols, nnz, stateptr, colptr, rowval, lower, upper, IMDP_F32,
+                                   (cudaStream_t)stream, &m, 0, -1, budget_per_iteration);
+  if (s != IMDP_OK) return s;
+  imdp_model* h = new imdp_model();
+  h->dev = m;
+  cudaGetDevice(&h->device);
+  *out = h;
+  return IMDP_OK;
+}
+
+imdp_status imdp_model_exact_columns(const imdp_model* m, int32_t* n_exact, int64_t* exact_entries,
+                                     double* budget_per_iteration) {
+  set_error("");
+  if (!m || !m->dev) { set_error("model is NULL"); return IMDP_EINVAL; }
+  if (n_exact) *n_exact = m->dev->n_exact;
+  if (exact_entries) *exact_entries = m->dev->exact_entries;
+  if (budget_per_iteration) *budget_per_iteration = m->dev->f32_budget;
+  return IMDP_OK;
+}
+
 imdp_status imdp_model_info(const imdp_model* m, int32_t* n_states, int32_t* n_cols, int64_t* nnz,
                             size_t* device_bytes, int32_t* max_col_nnz) {
   if (!m) { set_error("model is NULL"); return IMDP_EINVAL; }

@@ -192,6 +192,16 @@ IMDP_API imdp_status imdp_session_get_launch(const imdp_session* s, imdp_launch_
   return IMDP_OK;
 }
 
+IMDP_API imdp_status imdp_session_plan(const imdp_session* s, int32_t* n_tiles, int32_t* n_wide,
+                                      int64_t* wide_entries) {
+  set_error("");
+  if (!s || !s->s) { set_error("NULL session"); return IMDP_EINVAL; }
+  if (n_tiles) *n_tiles = s->s->n_tiles;
+  if (n_wide) *n_wide = s->s->n_wide;
+  if (wide_entries) *wide_entries = s->s->wide_entries;
+  return IMDP_OK;
+}
+
 IMDP_API imdp_status imdp_session_autotune(imdp_session* s, int32_t iters, const char* cache_path, void* stream,
                                            imdp_launch_config* chosen, double* ms_per_iter) {
   set_error("");

@@ -259,6 +259,13 @@ __device__ __forceinline__ uint64_t ld_value(const uint64_t* p) {
   asm volatile("ld.global.nc.L1::evict_last.u64 %0, [%1];" : "=l"(v) : "l"(p));
   return v;
 }
+// High 32 bits of a value word (the whole value of a problem on 32-bit
+// storage, whose values keep their low 32 bits zero).
+__device__ __forceinline__ uint32_t ld_value_hi(const uint64_t* p) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(v) : "l"(reinterpret_cast<const uint32_t*>(p) + 1));
+  return v;
+}
 
 // Destinations of one column in global memory (streamed loads); in shared
 // memory a plain pointer serves.
@@ -325,6 +332,42 @@ __device__ __forceinline__ void warm_pass(const typename RowsOf<gmem>::type rows
   }
 }
 
+// The warm pass on 32-bit storage, in 32-bit arithmetic. Values are the high
+// words vh (Q1.31) of value words whose low words are zero; bounds are the
+// column's mantissas m (value m 2^-(31+s), s = shift_j). Each product vh * m is
+// exact in 64 bits, and (vh * m) >> s equals the 64-bit routines' product
+// hi64((vh << 32) * (m << (32 - s))) exactly, so this pass gives the same acc,
+// and the same decisions from its gap sums (kept in mantissa units, where no
+// sum can wrap), as warm_pass on the widened bounds: one 32x32 multiply, a
+// shift and a 64-bit add per entry instead of a 64x64 multiply-high.
+template <bool gmem>
+__device__ __forceinline__ void warm_pass32(const typename RowsOf<gmem>::type rows, const uint2* __restrict__ m,
+                                            int32_t k, const uint64_t* __restrict__ V, uint32_t vk, int s, bool pess,
+                                            int lane, uint64_t& acc, uint64_t& flt, uint64_t& geq) {
+  const int nb = (k + 31) >> 5;
+#pragma unroll 2
+  for (int it = 0; it < nb; ++it) {
+    const int idx = it * 32 + lane;
+    const bool ok = idx < k;
+    const uint32_t v = ld_value_hi(V + (ok ? rows[idx] : 0));
+    uint2 b = make_uint2(0, 0);
+    if (ok) b = gmem ? ld_stream_u32x2(m + idx) : m[idx];
+    const bool below = pess ? (v < vk) : (v > vk);
+    const uint32_t g = below ? b.y : 0u;
+    acc += ((uint64_t)v * (uint64_t)(b.x + g)) >> s;
+    flt += g;
+    geq += v == vk ? b.y : 0u;
+  }
+}
+
+// floor(a * b / 2^s) for a < 2^32, b < 2^64, 0 <= s < 64.
+__device__ __forceinline__ uint64_t mul_shr(uint64_t a, uint64_t b, int s) {
+  const uint64_t lo = a * b, hi = __umul64hi(a, b);
+  return s ? (hi << (64 - s)) | (lo >> s) : lo;
+}
+// x << d, saturating at 2^64 - 1.
+__device__ __forceinline__ uint64_t shl_sat(uint64_t x, int d) { return (x >> (64 - d)) ? ~0ull : x << d; }
+
 // `rem_word` is rem = 1 - sum(lower) in Q1.63 (<= 2^63); when 0 < rem < 2^63 and
 // the column's gaps add up to < 2^64 ("narrow"), model creation sets bit 63 as a
 // flag on top of rem.
@@ -360,6 +403,23 @@ __device__ __forceinline__ bool column_warm(const typename RowsOf<gmem>::type ro
     return true;
   }
   if (hint < 0 || hint >= k) return false;
+  if (f32) {
+    // 32-bit storage: the pass in 32-bit arithmetic (same words as below)
+    const int down = lg.down, sh = 32 - down;
+    const uint32_t vk32 = ld_value_hi(V + rows[hint]);
+    uint64_t acc = 0, flt = 0, geq = 0;
+    warm_pass32<gmem>(rows, static_cast<const uint2*>(lg.p), k, V, vk32, sh, pess, lane, acc, flt, geq);
+    acc = warp_sum_u64(acc);
+    flt = warp_sum_u64(flt);
+    geq = warp_sum_u64(geq);
+    const uint64_t rem_m = rem >> down;  // exact: rem is a multiple of 2^down
+    if (flt < rem_m && rem_m - flt <= geq) {
+      *q = acc + mul_shr(vk32, rem_m - flt, sh);
+      return true;
+    }
+    *miss = WarmMiss{(uint64_t)vk32 << 32, acc, shl_sat(flt, down), shl_sat(geq, down), true};
+    return false;
+  }
   const uint64_t vk = ld_value(V + rows[hint]);
   uint64_t acc = 0, flt = 0, geq = 0;
   if (narrow_of(rem_word)) {
@@ -691,14 +751,20 @@ __device__ __forceinline__ void best_action(const Problem& P, int32_t jb, int32_
 // V_k(s) of a free state from the optimum over its actions (Q2.62): the
 // reachability value clamped at 1, or the reward update W_k = c_s + gamma T(W_{k-1})
 // in signed Q2.62, clamped to [0, 1].
+// A problem on 32-bit storage keeps its values at 32 bits (rounded to nearest,
+// low word zero), which its warm passes read as Q1.31.
 __device__ __forceinline__ uint64_t free_state_value(const Problem& P, int32_t s, uint64_t bestq) {
+  uint64_t v;
   if (P.property == kPropReward) {
     const int64_t tt = (int64_t)(__umul64hi(P.gamma_fix, bestq) << 1);
     int64_t w = P.rbias[s] + tt;
     w = w < 0 ? 0 : (w > (int64_t)(kOne >> 1) ? (int64_t)(kOne >> 1) : w);
-    return (uint64_t)w << 1;
+    v = (uint64_t)w << 1;
+  } else {
+    v = bestq >= (kOne >> 1) ? kOne : (bestq << 1);  // Q2.62 -> Q1.63, clamp at 1
   }
-  return bestq >= (kOne >> 1) ? kOne : (bestq << 1);  // Q2.62 -> Q1.63, clamp at 1
+  if (P.lg32) v = round_value32(v);
+  return v;
 }
 
 // State epilogue of a tile (one warp): opt over actions, reach/avoid mask,
@@ -740,6 +806,22 @@ __device__ __forceinline__ void stage_column(Stage& st, const Tile& T, int32_t l
   const int32_t eb = T.e0 & ~3, cb = T.c0 & ~3, mb = T.c0 & ~1;
   const int32_t ca = st.cptr[c - cb], ce = st.cptr[c + 1 - cb];
   const int32_t h = P.hint ? st.hint[c - cb] : -1;
+  if (f32 && P.xoff) {
+    // a correction column of 32-bit storage: its exact bounds are not staged,
+    // so it reads them (and its destinations) from global memory
+    const int32_t xo = __ldg(P.xoff + c);
+    if (xo >= 0) {
+      int32_t hout;
+      const uint64_t q = column_q<false, true>(GRows{P.rowval + ca}, Bounds<false, true>{P.lgx + xo, 0}, ce - ca,
+                                               st.rem[c - mb], P.V[(k_iter - 1) & 1], P.pessimistic != 0, ws, lane,
+                                               h, &hout);
+      if (lane == 0) {
+        st.q[li] = q;
+        if (P.hint && hout != h) P.hint[c] = hout;
+      }
+      return;
+    }
+  }
   Bounds<f32> bd;
   if (f32)
     bd = Bounds<f32>{reinterpret_cast<const uint2*>(st.lg) + (ca - (T.e0 & ~1)), 32 - st.shift[c - cb]};
@@ -755,6 +837,13 @@ __device__ __forceinline__ void stage_column(Stage& st, const Tile& T, int32_t l
 }
 
 __device__ void end_of_launch(const StepLaunch& L, int* is_last);
+
+// Tiles this launch visits: the running prefix recorded by the previous launch.
+__device__ __forceinline__ int32_t tiles_to_visit(const StepLaunch& L) {
+  const int32_t lim = L.ctl->tile_limit;
+  return lim > 0 && lim - 1 < L.n_tiles ? lim - 1 : L.n_tiles;
+}
+
 
 template <int W>
 __global__ void __launch_bounds__(32 * (W + 1), 1) bellman_step_kernel(StepLaunch L) {
@@ -781,7 +870,8 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) bellman_step_kernel(StepLaunc
       bool ok = true;
       int pending_round[kStages];
       for (int s = 0; s < kStages; ++s) pending_round[s] = -1;
-      for (int32_t t = blockIdx.x; t < L.n_tiles; t += gridDim.x, ++i) {
+      const int32_t nt = tiles_to_visit(L);
+      for (int32_t t = blockIdx.x; t < nt; t += gridDim.x, ++i) {
         const int stage = i % kStages, round = i / kStages;
         if (round > 0 && !wait_phase(&S.empty[stage], (round - 1) & 1, err, false)) {
           ok = false;
@@ -855,7 +945,8 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) bellman_step_kernel(StepLaunc
     WarpScratch* ws = &S.ws[warp];
     int32_t slot_base = 0;  // global slot index of tile j's first slot
     int j = 0;
-    for (int32_t t = blockIdx.x; t < L.n_tiles; t += gridDim.x, ++j) {
+    const int32_t nt = tiles_to_visit(L);  // the producer visits the same tiles
+    for (int32_t t = blockIdx.x; t < nt; t += gridDim.x, ++j) {
       const int stage = j % kStages, round = j / kStages;
       int got = 1;
       if (lane == 0) got = wait_phase(&S.full[stage], round & 1, err, false) ? 1 : 0;
@@ -937,7 +1028,7 @@ __device__ void end_of_launch(const StepLaunch& L, int* is_last) {
     if (PQ.infinite) {
       const unsigned long long r = it->resmax;
       it->resmax = 0;
-      if (r < PQ.eps_fix) {
+      if (r < PQ.eps_fix && !PQ.external_stop) {
         it->done = 1;
         it->k_final = kq;
       } else if (kq >= PQ.horizon) {
@@ -954,8 +1045,21 @@ __device__ void end_of_launch(const StepLaunch& L, int* is_last) {
     L.ctl->finished = 0;
     L.ctl->wide_next = 0;
     L.ctl->tile_next = 0;
+    *is_last = -1;  // reused below: the largest rank still running
   }
+  if (!L.rank_of) return;
+  // Tiles are laid out by rank, so the next launch needs only the prefix that
+  // belongs to problems still running (a finished problem's tiles are never
+  // visited again).
+  __syncthreads();
+  int rmax = -1;
+  for (int q = threadIdx.x; q < L.count; q += blockDim.x)
+    if (!L.its[q].done) rmax = max(rmax, L.rank_of[q]);
+  if (rmax >= 0) atomicMax(is_last, rmax);
+  __syncthreads();
+  if (threadIdx.x == 0) L.ctl->tile_limit = (*is_last >= 0 ? L.rank_tile_end[*is_last] : 0) + 1;
 }
+
 
 
 // ---------------------------------------------------------------- direct kernel
@@ -971,10 +1075,19 @@ __device__ void end_of_launch(const StepLaunch& L, int* is_last) {
 // directly. Each column runs the same exact routines as in the ring kernel,
 // so both kernels give the same words.
 
+// Bulk prefetch of [p, p + bytes) into L2, widened to 16-byte boundaries (the
+// model's arrays are padded so that such windows stay inside them).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  const uintptr_t a = (uintptr_t)p & ~(uintptr_t)15;
+  const uintptr_t e = ((uintptr_t)p + bytes + 15) & ~(uintptr_t)15;
+  if (e > a)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a)) : "memory");
+}
+
 // Column metadata of 32 consecutive columns, one per lane.
 struct ColChunk {
   int32_t base = -1;
-  int32_t ca = 0, ce = 0, hint = -1, shift = 0;
+  int32_t ca = 0, ce = 0, hint = -1, shift = 0, xoff = -1;
   uint64_t rem = 0;
 };
 
@@ -1020,19 +1133,36 @@ __device__ void direct_tile(const StepLaunch& L, const Tile& T, int32_t k_iter, 
               cc.ce = __ldg(colptr + mc + 1);
               cc.rem = __ldg(P.rem + mc);
               cc.hint = hint ? hint[mc] : -1;
-              if (f32) cc.shift = __ldg(P.shift + mc);
+              if (f32) {
+                cc.shift = __ldg(P.shift + mc);
+                cc.xoff = P.xoff ? __ldg(P.xoff + mc) : -1;
+              }
             }
           }
           const int src = c - cc.base;
           const int32_t ca = __shfl_sync(kFull, cc.ca, src), ce = __shfl_sync(kFull, cc.ce, src);
+          // start pulling the next column of the chunk into L2 while this one runs
+          // (its bounds and destinations are contiguous after this column's)
+          const int32_t cn = src + 1 < 32 ? __shfl_sync(kFull, cc.ce, src + 1) : ce;
+          if (lane == 0 && cn > ce && c + 1 < T.c1) {
+            prefetch_l2(P.rowval + ce, (size_t)(cn - ce) * sizeof(int32_t));
+            if (f32)
+              prefetch_l2(P.lg32 + ce, (size_t)(cn - ce) * sizeof(uint2));
+            else
+              prefetch_l2(P.lg + ce, (size_t)(cn - ce) * sizeof(ulonglong2));
+          }
           const int32_t h = __shfl_sync(kFull, cc.hint, src);
           const uint64_t rw = __shfl_sync(kFull, cc.rem, src);
           int32_t hout;
           uint64_t q;
-          if (f32)
+          const int32_t xo = f32 ? __shfl_sync(kFull, cc.xoff, src) : -1;
+          if (f32 && xo < 0)
             q = column_q<true, true>(GRows{P.rowval + ca},
                                      Bounds<true, true>{P.lg32 + ca, 32 - __shfl_sync(kFull, cc.shift, src)}, ce - ca,
                                      rw, Vin, pess, ws, lane, h, &hout);
+          else if (f32)  // correction column: its exact bounds
+            q = column_q<false, true>(GRows{P.rowval + ca}, Bounds<false, true>{P.lgx + xo, 0}, ce - ca, rw, Vin,
+                                      pess, ws, lane, h, &hout);
           else
             q = column_q<false, true>(GRows{P.rowval + ca}, Bounds<false, true>{P.lg + ca, 0}, ce - ca, rw, Vin, pess,
                                       ws, lane, h, &hout);
@@ -1056,11 +1186,12 @@ __global__ void __launch_bounds__(32 * NW, MINB) bellman_direct_kernel(StepLaunc
   __shared__ int is_last;
   const int lane = threadIdx.x & 31;
   WarpScratch* ws = &ws_all[threadIdx.x >> 5];
+  const int32_t nt = tiles_to_visit(L);
   for (;;) {
     int32_t t = 0;
     if (lane == 0) t = (int32_t)atomicAdd(&L.ctl->tile_next, 1u);
     t = __shfl_sync(kFull, t, 0);
-    if (t >= L.n_tiles) break;
+    if (t >= nt) break;
     const Tile T = L.tiles[t];
     int32_t k_iter;
     if (!problem_active(L, T.p, &k_iter)) continue;
@@ -1493,9 +1624,13 @@ __global__ void __launch_bounds__(kWideThreads, 6) bellman_wide_kernel(StepLaunc
         const int32_t h = P.hint ? P.hint[c] : -1;
         int32_t hout;
         uint64_t q;
-        if (P.lg32)
+        const int32_t xo = P.xoff ? __ldg(P.xoff + c) : -1;
+        if (P.lg32 && xo < 0)
           q = wide_column_q<true>(P.rowval + ca, Bounds<true>{P.lg32 + ca, 32 - __ldg(P.shift + c)}, ce - ca,
                                   __ldg(P.rem + c), Vin, pess, h, &hout, W);
+        else if (P.lg32)  // correction column: its exact bounds
+          q = wide_column_q<false>(P.rowval + ca, Bounds<false>{P.lgx + xo, 0}, ce - ca, __ldg(P.rem + c), Vin, pess,
+                                   h, &hout, W);
         else
           q = wide_column_q<false>(P.rowval + ca, Bounds<false>{P.lg + ca, 0}, ce - ca, __ldg(P.rem + c), Vin, pess,
                                    h, &hout, W);

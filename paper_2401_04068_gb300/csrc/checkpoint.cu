@@ -97,6 +97,9 @@ IMDP_API imdp_status imdp_session_restore(imdp_session* s, int32_t index, const 
   // the saved hints belong to the interrupted run: start this problem without any
   if (e == cudaSuccess)
     e = cudaMemsetAsync(P.hint, 0xff, sizeof(int32_t) * padded_i32((size_t)S->models[index]->n_cols), st);
+  // the problem may run again: the next launch visits every tile (the running
+  // prefix is recomputed when it ends)
+  if (e == cudaSuccess) e = cudaMemsetAsync(&S->ctl->tile_limit, 0, sizeof(int32_t), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // `it` lives on this stack frame
   if (e != cudaSuccess) return cuda_status(e, "restore");
   // The session's launch count since its reset bounds how many more launches

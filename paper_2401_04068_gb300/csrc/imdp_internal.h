@@ -25,6 +25,12 @@ namespace imdp {
 
 constexpr uint64_t kOne = 1ull << 63;  // 1.0 in Q1.63
 
+// A value in [0, 1] (Q1.63) rounded to nearest at 32 bits (low word zero):
+// the values of a problem on 32-bit storage.
+__host__ __device__ __forceinline__ uint64_t round_value32(uint64_t v) {
+  return v >= kOne - (1ull << 31) ? kOne : (v + (1ull << 31)) & ~0xffffffffull;
+}
+
 // Property kinds inside the kernels.
 enum : int32_t { kPropReach = 0, kPropReachAvoid = 1, kPropReward = 2 };
 
@@ -60,7 +66,13 @@ struct DevModel {
   ulonglong2* lg = nullptr;     // IMDP_F64: nnz x {lower, gap = upper - lower} in Q1.63
   uint2* lg32 = nullptr;        // IMDP_F32: nnz x {lower, gap} as 32-bit mantissas, value = m * 2^-(31 + shift_j)
   int32_t* shift = nullptr;     // IMDP_F32: per-column shift_j (padded like colptr)
-  double err_bound = 0.0;       // IMDP_F32: max over columns of sum |dlower| + |dupper| (per-iteration error bound)
+  int32_t* xoff = nullptr;      // IMDP_F32: per column, offset of its exact bounds in lgx (-1: 32-bit column);
+                                // nullptr when every column is 32-bit
+  ulonglong2* lgx = nullptr;    // IMDP_F32: exact {lower, gap} of the correction columns (compact)
+  int32_t n_exact = 0;          // IMDP_F32: correction columns
+  int64_t exact_entries = 0;    //           and their transitions
+  double f32_budget = 0.0;      // IMDP_F32: the per-iteration budget the columns were sorted by
+  double err_bound = 0.0;       // IMDP_F32: guaranteed per-iteration error bound (see imdp_model_error_bound)
   uint64_t* rem = nullptr;      // n_cols: 1 - sum(lower) in Q1.63 (clamped at 0)
   size_t bytes = 0;
   std::vector<int32_t> h_stateptr;  // host copies of the structure (tile planning)
@@ -85,6 +97,8 @@ struct alignas(16) Problem {
   const uint64_t* rem;
   const uint2* lg32;      // 32-bit storage (nullptr for 64-bit models)
   const int32_t* shift;   // per-column shift of the 32-bit storage
+  const int32_t* xoff;    // 32-bit storage: per column, offset of its exact bounds in lgx (-1: 32-bit); nullable
+  const ulonglong2* lgx;  // 32-bit storage: exact bounds of the correction columns
   const uint8_t* fixed;   // n_states: 0 free, 1 held at 1 (reach target), 2 held at 0 (avoid)
   uint64_t* V[2];         // ping-pong value buffers; iteration k writes V[k & 1]
   int32_t* policy;        // nullable; see policy_mode
@@ -97,7 +111,7 @@ struct alignas(16) Problem {
   int32_t horizon;        // K (finite) or iteration cap (infinite)
   int32_t infinite;
   int32_t policy_mode;    // 0 none, 1 time-dependent K x n, 2 stationary n
-  int32_t _pad;
+  int32_t external_stop;  // infinite horizon on a slice: the caller tests the residual of all slices
   uint64_t eps_fix;       // infinite horizon: stop when max |dV| < eps_fix
   uint64_t gamma_fix;     // reward: discount in Q1.63
 };
@@ -116,6 +130,7 @@ struct StepControl {
   unsigned int error;      // nonzero: a bounded wait inside the kernel gave up
   unsigned int wide_next;  // next wide state to take in the running launch
   unsigned int tile_next;  // next tile to take in the running launch (direct kernel)
+  int32_t tile_limit;      // 0: every tile; t + 1: only tiles [0, t) belong to running problems
 };
 
 // Launch configuration of the Bellman step (per session; chosen by rule or by
@@ -162,6 +177,11 @@ struct StepLaunch {
   int32_t n_wide;
   const int2* wide;  // (problem, state) of every wide state
   int64_t tile_cols;   // columns in all tiles (the launcher picks the CTA shape from it)
+  // Tiles laid out by problem rank (longest horizon first; nullable): after a
+  // launch, the tiles of running problems are a prefix, [0, rank_tile_end[r])
+  // with r the largest rank still running.
+  const int32_t* rank_of;        // count: rank of each problem
+  const int32_t* rank_tile_end;  // count: tiles of ranks 0..r
   int32_t grid_total;  // CTAs of both step kernels in this launch (set by the launcher)
   int32_t stall;       // test hook: the producer issues nothing, so every wait runs out
 };
@@ -197,10 +217,13 @@ void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out, std:
                 int32_t tile_entries = 0, int32_t wide_col = 0);
 
 // model.cu
+// Per-iteration error budget of 32-bit storage when the caller names none:
+// 1e-6 over the paper's benchmark horizon of K = 200 iterations.
+constexpr double kDefaultF32Budget = 5e-9;
 imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, const int32_t* stateptr,
                              const int32_t* colptr, const int32_t* rowval, const double* lower,
                              const double* upper, imdp_dtype dtype, cudaStream_t st, DevModel** out,
-                             int32_t own0 = 0, int32_t own1 = -1);
+                             int32_t own0 = 0, int32_t own1 = -1, double budget = kDefaultF32Budget);
 void model_destroy(DevModel* m);
 inline bool is_slice(const DevModel* m) { return m->own0 != 0 || m->own1 != m->n_states; }
 
@@ -219,6 +242,9 @@ struct Session {
   std::vector<Problem> probs_h;
   std::vector<int32_t> base_h;
   std::vector<int64_t> policy_cells;
+  std::vector<int32_t> order;             // problems by rank: longest horizon (infinite) first
+  int32_t* rank_of = nullptr;             // device copies for the running-prefix bound
+  int32_t* rank_tile_end = nullptr;
   std::vector<double> v_offset, v_scale;  // V = offset + scale * W (reward: affine map; reach: 0, 1)
   std::vector<uint64_t*> w0;              // reward: device copy of W_0 for resets (nullptr otherwise)
   int32_t* hints = nullptr;               // sum of n_cols: threshold hints of every problem
@@ -235,6 +261,7 @@ struct Session {
   int32_t n_tiles = 0;
   int2* wide = nullptr;
   int32_t n_wide = 0;
+  int64_t wide_entries = 0;  // transitions of the wide states (host count)
   SideStream side;  // created when the session has both tiles and wide states
   LaunchConfig cfg;  // launch configuration (rule, set_launch or the autotuner)
   StepLaunch L{};

@@ -89,7 +89,7 @@ __global__ void convert_columns_kernel(int32_t n_states, int32_t n_cols, const i
 // total rounding error sum |dlower| + |dupper| is reported.
 __global__ void quantize_columns_kernel(int32_t n_cols, const int32_t* __restrict__ colptr,
                                         const ulonglong2* __restrict__ lg, uint2* __restrict__ lg32,
-                                        int32_t* __restrict__ shift, uint64_t* __restrict__ rem,
+                                        int32_t* __restrict__ shift, uint64_t* __restrict__ rem32,
                                         double* __restrict__ err) {
   const int lane = threadIdx.x & 31;
   const int32_t warps = gridDim.x * (blockDim.x >> 5);
@@ -133,9 +133,29 @@ __global__ void quantize_columns_kernel(int32_t n_cols, const int32_t* __restric
     }
     if (lane == 0) {
       shift[j] = sh;
-      rem[j] = rem_word(lsum, gsum);
+      rem32[j] = rem_word(lsum, gsum);
       err[j] = e / 9223372036854775808.0;
     }
+  }
+}
+
+// Correction columns of 32-bit storage: a column whose rounding error is above
+// the budget keeps its 64-bit bounds, copied to lgx[xoff[j] ...], and its exact
+// rem word; every other column takes the 32-bit rem word (one warp per column).
+__global__ void select_columns_kernel(int32_t n_cols, const int32_t* __restrict__ colptr,
+                                      const ulonglong2* __restrict__ lg, const int32_t* __restrict__ xoff,
+                                      ulonglong2* __restrict__ lgx, const uint64_t* __restrict__ rem32,
+                                      uint64_t* __restrict__ rem) {
+  const int lane = threadIdx.x & 31;
+  const int32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (int32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n_cols; j += warps) {
+    const int32_t x = xoff[j];
+    if (x < 0) {
+      if (lane == 0) rem[j] = rem32[j];
+      continue;
+    }
+    const int32_t a = colptr[j], b = colptr[j + 1];
+    for (int32_t i = a + lane; i < b; i += 32) lgx[x + (i - a)] = lg[i];
   }
 }
 
@@ -183,7 +203,7 @@ void model_destroy(DevModel* m) {
   // that may still read them (what cudaFree would do) before handing them back
   cudaDeviceSynchronize();
   for (void* p : {(void*)m->stateptr, (void*)m->colptr, (void*)m->rowval, (void*)m->lg, (void*)m->rem,
-                  (void*)m->tiles, (void*)m->wide, (void*)m->lg32, (void*)m->shift})
+                  (void*)m->tiles, (void*)m->wide, (void*)m->lg32, (void*)m->shift, (void*)m->xoff, (void*)m->lgx})
     if (p) cudaFreeAsync(p, nullptr);
   cudaStreamSynchronize(nullptr);
   delete m;
@@ -220,8 +240,12 @@ bool pool_alloc(T** p, size_t bytes, cudaStream_t st) {
 imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, const int32_t* stateptr,
                              const int32_t* colptr, const int32_t* rowval, const double* lower,
                              const double* upper, imdp_dtype dtype, cudaStream_t st, DevModel** out,
-                             int32_t own0, int32_t own1) {
+                             int32_t own0, int32_t own1, double budget) {
   TraceRange trace("imdp model create");
+  if (!(budget >= 0.0)) {
+    set_error("the per-iteration error budget of 32-bit storage must be >= 0");
+    return IMDP_EINVAL;
+  }
   if (!out) { set_error("out is NULL"); return IMDP_EINVAL; }
   *out = nullptr;
   if (own1 < 0) own1 = n_states;
@@ -339,11 +363,15 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
     return IMDP_EINFEASIBLE;
   }
   if (dtype == IMDP_F32) {
-    // re-encode the bounds in 32 bits and drop the 64-bit copy
+    // Re-encode the bounds in 32 bits and drop the 64-bit copy, except for the
+    // correction columns: those whose rounding error (plus the rounding of the
+    // values to 32 bits) would exceed the per-iteration budget keep their exact
+    // bounds in a compact 64-bit array and run the 64-bit routines.
     const size_t nz32 = ((nz + 1) & ~size_t(1)) + 2;  // padded for 16-byte bulk-copy windows
-    DevBuf derr2;
+    DevBuf derr2, drem32;
     if (!pool_alloc(&m->lg32, sizeof(uint2) * nz32, st) || !pool_alloc(&m->shift, sizeof(int32_t) * nc_pad, st) ||
-        !derr2.alloc(sizeof(double) * n_cols, st)) {
+        !pool_alloc(&m->xoff, sizeof(int32_t) * nc_pad, st) || !derr2.alloc(sizeof(double) * n_cols, st) ||
+        !drem32.alloc(sizeof(uint64_t) * std::max<size_t>(n_cols, 1), st)) {
       cudaGetLastError();
       model_destroy(m);
       set_error("device allocation failed for 32-bit storage");
@@ -352,8 +380,8 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
     e = cudaMemsetAsync(m->lg32, 0, sizeof(uint2) * nz32, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->shift, 0, sizeof(int32_t) * nc_pad, st);
     if (e == cudaSuccess) {
-      quantize_columns_kernel<<<grid, 256, 0, st>>>(n_cols, m->colptr, m->lg, m->lg32, m->shift, m->rem,
-                                                    (double*)derr2.p);
+      quantize_columns_kernel<<<grid, 256, 0, st>>>(n_cols, m->colptr, m->lg, m->lg32, m->shift,
+                                                    (uint64_t*)drem32.p, (double*)derr2.p);
       e = cudaGetLastError();
     }
     std::vector<double> herrs(n_cols);
@@ -361,10 +389,47 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
       e = cudaMemcpyAsync(herrs.data(), derr2.p, sizeof(double) * n_cols, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { model_destroy(m); return cuda_status(e, "32-bit storage"); }
-    for (double x : herrs) m->err_bound = std::max(m->err_bound, x);
+    // per-iteration error of a 32-bit column: its rounding plus the rounding of
+    // the values to 32 bits (products are exact to 2^-62, counted below)
+    const double vround = std::ldexp(1.0, -32);
+    std::vector<int32_t> xo(nc_pad, -1);
+    int64_t xn = 0;
+    double worst32 = 0.0;
+    for (int32_t j = 0; j < n_cols; ++j) {
+      if (herrs[j] + vround > budget) {
+        xo[j] = (int32_t)xn;
+        xn += hc[j + 1] - hc[j];
+        ++m->n_exact;
+      } else {
+        worst32 = std::max(worst32, herrs[j]);
+      }
+    }
+    if (xn >= (int64_t(1) << 31)) { model_destroy(m); set_error("too many correction entries"); return IMDP_EINVAL; }
+    m->exact_entries = xn;
+    m->err_bound = worst32 + vround + std::ldexp((double)m->max_col + 1.0, -62);
+    m->f32_budget = budget;
+    if (xn > 0 && !pool_alloc(&m->lgx, sizeof(ulonglong2) * (size_t)xn, st)) {
+      cudaGetLastError();
+      model_destroy(m);
+      set_error("device allocation failed for the correction columns");
+      return IMDP_ENOMEM;
+    }
+    e = cudaMemcpyAsync(m->xoff, xo.data(), sizeof(int32_t) * nc_pad, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+      select_columns_kernel<<<grid, 256, 0, st>>>(n_cols, m->colptr, m->lg, m->xoff, m->lgx,
+                                                  (const uint64_t*)drem32.p, m->rem);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // `xo` is a host staging vector
+    if (e != cudaSuccess) { model_destroy(m); return cuda_status(e, "32-bit storage"); }
     cudaFreeAsync(m->lg, st);
     m->lg = nullptr;
-    m->bytes = m->bytes - sizeof(ulonglong2) * nz + sizeof(uint2) * nz32 + sizeof(int32_t) * nc_pad;
+    if (m->n_exact == 0) {  // no correction column: nothing reads the offsets
+      cudaFreeAsync(m->xoff, st);
+      m->xoff = nullptr;
+    }
+    m->bytes = m->bytes - sizeof(ulonglong2) * nz + sizeof(uint2) * nz32 + sizeof(int32_t) * nc_pad +
+               (m->xoff ? sizeof(int32_t) * nc_pad : 0) + sizeof(ulonglong2) * (size_t)xn;
   }
   m->h_stateptr = std::move(hs);
   m->h_colptr = std::move(hc);

@@ -146,6 +146,8 @@ extern "C" IMDP_API imdp_status imdp_value_iteration_noalloc(imdp_model* m, cons
   P.rem = dm->rem;
   P.lg32 = dm->lg32;
   P.shift = dm->shift;
+  P.xoff = dm->xoff;
+  P.lgx = dm->lgx;
   P.fixed = d_mask;
   P.V[0] = d_V;
   P.V[1] = d_V + n;
@@ -184,7 +186,7 @@ extern "C" IMDP_API imdp_status imdp_value_iteration_noalloc(imdp_model* m, cons
   noalloc_init_kernel<<<g, 256, 0, st>>>(n, d_mask, d_V);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e, "noalloc init");
 
-  StepLaunch L;
+  StepLaunch L{};
   L.probs = d_prob;
   L.its = d_it;
   L.state_base = d_base;

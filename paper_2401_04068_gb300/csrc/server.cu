@@ -187,6 +187,8 @@ struct Server {
     P.rem = m->rem;
     P.lg32 = m->lg32;
     P.shift = m->shift;
+    P.xoff = m->xoff;
+    P.lgx = m->lgx;
     P.fixed = mask;
     P.V[0] = V;
     P.V[1] = V + n;
@@ -219,6 +221,7 @@ struct Server {
         ch[s] = (int64_t)std::llround((r->reward[s] - lo * (1.0 - sp->discount)) / D * 4611686018427387904.0);
         const double ws = std::min(1.0, std::max(0.0, (r->reward[s] - lo) / D));
         wh[s] = (uint64_t)std::llround(ws * 4611686018427387904.0) << 1;
+        if (m->lg32) wh[s] = round_value32(wh[s]);  // values of 32-bit storage keep 32 bits
       }
       if (e == cudaSuccess) e = cudaMemcpyAsync(c, ch.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, stream);
       if (e == cudaSuccess) e = cudaMemcpyAsync(V, wh.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, stream);

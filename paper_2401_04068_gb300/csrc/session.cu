@@ -93,10 +93,6 @@ imdp_status check_spec(const DevModel* m, const imdp_spec* sp) {
       }
   }
   if (sp->horizon < 0) { set_error("horizon must be >= 0"); return IMDP_EINVAL; }
-  if (sp->infinite_time && is_slice(m)) {
-    // each slice would test convergence on its own states only
-    set_error("a state-sharded slice runs finite horizons only"); return IMDP_EINVAL;
-  }
   if (sp->infinite_time && !(sp->eps > 0.0)) { set_error("eps must be > 0 for an infinite horizon"); return IMDP_EINVAL; }
   if (sp->n_reach < 0 || (sp->n_reach > 0 && !sp->reach)) { set_error("bad reach set"); return IMDP_EINVAL; }
   if (sp->property == IMDP_REACH_AVOID && (sp->n_avoid < 0 || (sp->n_avoid > 0 && !sp->avoid))) {
@@ -159,14 +155,25 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   S->v_offset.assign(count, 0.0);
   S->v_scale.assign(count, 1.0);
   S->w0.assign(count, nullptr);
+  // rank problems by horizon, longest first (infinite horizons first of all):
+  // tiles laid out in this order leave the finished problems' tiles at the end
+  S->order.resize(count);
+  for (int p = 0; p < count; ++p) S->order[p] = p;
+  std::stable_sort(S->order.begin(), S->order.end(), [&](int a, int b) {
+    const int64_t ka = specs[a]->infinite_time ? INT64_MAX : specs[a]->horizon;
+    const int64_t kb = specs[b]->infinite_time ? INT64_MAX : specs[b]->horizon;
+    return ka > kb;
+  });
   std::vector<Tile> tiles;
   std::vector<int2> wide;
-  for (int p = 0; p < count; ++p) {
+  for (int p : S->order) {
     const size_t at = tiles.size();
     tiles.insert(tiles.end(), ms[p]->h_tiles.begin(), ms[p]->h_tiles.end());
     for (size_t t = at; t < tiles.size(); ++t) tiles[t].p = p;
     for (int32_t s : ms[p]->h_wide) wide.push_back(make_int2(p, s));
   }
+  S->rank_of = S->alloc<int32_t>(count);
+  S->rank_tile_end = S->alloc<int32_t>(count);
   // each problem's hint block starts on a 16-byte boundary and is padded, so
   // the kernel's bulk copies of hint windows stay aligned and in bounds
   for (int p = 0; p < count; ++p) S->total_cols += (int64_t)padded_i32(ms[p]->n_cols);
@@ -177,7 +184,8 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   S->probs = S->alloc<Problem>(count);
   S->its = S->alloc<IterState>(count);
   S->ctl = S->alloc<StepControl>(1);
-  if (!S->hints || !S->fixed || !S->V || !S->base || !S->probs || !S->its || !S->ctl) {
+  if (!S->hints || !S->fixed || !S->V || !S->base || !S->probs || !S->its || !S->ctl || !S->rank_of ||
+      !S->rank_tile_end) {
     delete S; set_error("device allocation failed (session)"); return IMDP_ENOMEM;
   }
   S->probs_h.resize(count);
@@ -195,6 +203,8 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
     P.rem = m->rem;
     P.lg32 = m->lg32;
     P.shift = m->shift;
+    P.xoff = m->xoff;
+    P.lgx = m->lgx;
     P.fixed = S->fixed + S->base_h[p];
     P.hint = S->hints + col_off;
     col_off += (int64_t)padded_i32(m->n_cols);
@@ -205,6 +215,9 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
     P.maximize = sp->maximize ? 1 : 0;
     P.property = sp->property;
     P.infinite = sp->infinite_time ? 1 : 0;
+    // a slice holds part of the states: its own residual decides nothing, the
+    // caller stops it on the residual of all slices (imdp_session_residual)
+    P.external_stop = (P.infinite && is_slice(m)) ? 1 : 0;
     P.horizon = sp->infinite_time ? (sp->horizon > 0 ? sp->horizon : 1000000) : sp->horizon;
     P.eps_fix = sp->infinite_time ? eps_to_fixed(sp->eps) : 0;
     if (sp->property == IMDP_REWARD) {
@@ -222,6 +235,7 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
         c[s] = (int64_t)std::llround(cs * 4611686018427387904.0);
         const double ws = std::min(1.0, std::max(0.0, (sp->reward[s] - lo) / D));
         w[s] = (uint64_t)std::llround(ws * 4611686018427387904.0) << 1;
+        if (m->lg32) w[s] = round_value32(w[s]);  // values of 32-bit storage keep 32 bits
       }
       int64_t* d_c = S->alloc<int64_t>(n);
       uint64_t* d_w = S->alloc<uint64_t>(n);
@@ -285,8 +299,25 @@ imdp_status Session::install_plan(const std::vector<Tile>& tl, const std::vector
     e = cudaMemcpyAsync(wide, wl.data(), sizeof(int2) * wl.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors belong to the caller
   if (e != cudaSuccess) return cuda_status(e, "session plan");
+  // tiles of ranks 0..r (the plan lists problems in rank order)
+  std::vector<int32_t> rank(count), end(count, 0);
+  for (int r = 0; r < count; ++r) rank[order[r]] = r;
+  for (const Tile& T : tl) ++end[rank[T.p]];
+  for (int r = 1; r < count; ++r) end[r] += end[r - 1];
+  e = cudaMemcpyAsync(rank_of, rank.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rank_tile_end, end.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&ctl->tile_limit, 0, sizeof(int32_t), st);  // every tile, until a launch ends
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "session plan");
+  L.rank_of = rank_of;
+  L.rank_tile_end = rank_tile_end;
   n_tiles = (int32_t)tl.size();
   n_wide = (int32_t)wl.size();
+  wide_entries = 0;
+  for (const int2& w : wl) {
+    const DevModel* m = models[w.x];
+    wide_entries += m->h_colptr[m->h_stateptr[w.y + 1]] - m->h_colptr[m->h_stateptr[w.y]];
+  }
   L.tiles = tiles;
   L.n_tiles = n_tiles;
   L.wide = wide;
@@ -307,7 +338,7 @@ imdp_status Session::set_launch(const LaunchConfig& c, cudaStream_t st) {
   if (now.tile_entries != old.tile_entries || now.wide_col != old.wide_col) {
     std::vector<Tile> tl;
     std::vector<int2> wl;
-    for (int p = 0; p < count; ++p) {
+    for (int p : order) {
       std::vector<int32_t> ws;
       const size_t at = tl.size();
       plan_tiles(models[p], p, tl, ws, now.tile_entries, now.wide_col);
@@ -397,6 +428,12 @@ imdp_status Session::read_states(std::vector<IterState>& out, cudaStream_t st) {
 }
 
 imdp_status Session::run(int32_t check_every, cudaStream_t st) {
+  for (const Problem& P : probs_h)
+    if (P.external_stop) {
+      set_error("an infinite horizon on a state-sharded slice stops on the residual of every slice: step it and "
+                "test imdp_session_residual across the slices");
+      return IMDP_EINVAL;
+    }
   if (!any_infinite) {
     // Every problem finishes within max_horizon launches of the reset.
     return step(std::max<int32_t>(0, max_horizon - (int32_t)std::min<int64_t>(launched_since_reset, max_horizon)), st);

@@ -40,9 +40,58 @@ imdp_status values_window(imdp_session* s, int32_t index, int32_t k, int32_t s0,
   return IMDP_OK;
 }
 
+// max |V_k - V_{k-1}| over a range of raw iterates (one atomic per warp).
+__global__ void range_residual_kernel(int32_t n, const uint64_t* __restrict__ a, const uint64_t* __restrict__ b,
+                                      unsigned long long* __restrict__ out) {
+  unsigned long long m = 0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint64_t x = a[i], y = b[i];
+    const unsigned long long d = x > y ? x - y : y - x;
+    m = d > m ? d : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = t > m ? t : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 }  // namespace
 
 extern "C" {
+
+IMDP_API imdp_status imdp_session_residual(imdp_session* s, int32_t index, int32_t k, int32_t s0, int32_t s1,
+                                           uint64_t* dst, void* stream) {
+  set_error("");
+  uint64_t* cur = nullptr;
+  imdp_status st = values_window(s, index, k, s0, s1, &cur);
+  if (st != IMDP_OK) return st;
+  if (k < 1) { set_error("the residual needs k >= 1"); return IMDP_EINVAL; }
+  if (!dst || !is_device_pointer(dst)) { set_error("dst must be device memory"); return IMDP_EINVAL; }
+  uint64_t* prev = nullptr;
+  values_window(s, index, k - 1, s0, s1, &prev);
+  DeviceScope g(s->s->device);
+  const cudaStream_t st_ = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(dst, 0, sizeof(uint64_t), st_);
+  const int32_t n = s1 - s0;
+  if (e == cudaSuccess && n > 0) {
+    range_residual_kernel<<<std::min((n + 255) / 256, 1024), 256, 0, st_>>>(n, cur, prev, (unsigned long long*)dst);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? IMDP_OK : cuda_status(e, "residual");
+}
+
+IMDP_API imdp_status imdp_session_stop_threshold(const imdp_session* s, int32_t index, uint64_t* eps_raw) {
+  set_error("");
+  if (!s || !s->s || !eps_raw) { set_error("NULL argument"); return IMDP_EINVAL; }
+  if (index < 0 || index >= s->s->count) { set_error("problem index out of range"); return IMDP_EINVAL; }
+  const Problem& P = s->s->probs_h[index];
+  if (!P.infinite) { set_error("the problem has a finite horizon"); return IMDP_EINVAL; }
+  *eps_raw = P.eps_fix;
+  return IMDP_OK;
+}
+
 
 IMDP_API imdp_status imdp_partition_states(int32_t n_states, const int32_t* stateptr, const int32_t* colptr,
                                            int32_t n_parts, int32_t* bounds) {

@@ -40,14 +40,19 @@ def _run(model, m, spec, cfg, steps):
     return raw, k, V, resolved
 
 
-@pytest.mark.parametrize("case", ["reach", "reach_avoid_opt", "reward", "infinite", "f32", "mixed_wide"])
+@pytest.mark.parametrize("case", ["reach", "reach_avoid_opt", "reward", "infinite", "f32", "f32_pure", "mixed_wide"])
 def test_every_launch_config_gives_the_same_words(case):
     if case == "mixed_wide":
         # short, medium and long columns in one model: tiles and wide states
         m = banded_imdp(900, 2, 900 * 2 * 180 + 900 * 2 + 1, eps=0.1, seed=61)
     else:
         m = banded_imdp(700, 3, 700 * 3 * 40 + 700 * 3 + 1, eps=0.1, seed=60)
-    model = g.create_model(m, dtype=g.IMDP_F32 if case == "f32" else g.IMDP_F64)
+    if case == "f32":  # a budget small enough to keep some columns exact
+        model = g.create_model(m, dtype=g.IMDP_F32, budget=1.5e-9)
+    elif case == "f32_pure":  # no correction column: the ring kernel runs it too
+        model = g.create_model(m, dtype=g.IMDP_F32, budget=1.0)
+    else:
+        model = g.create_model(m)
     K = 40
     okw = dict(horizon=K, reach=m.goal)
     if case == "reach_avoid_opt":
@@ -60,6 +65,8 @@ def test_every_launch_config_gives_the_same_words(case):
         okw = dict(infinite_time=True, eps=1e-8, horizon=5000, reach=m.goal)
     spec = g.make_spec(**okw)
     steps = 5000 if case == "infinite" else K
+    if case == "f32":
+        assert g.imdp_model_exact_columns(model)[0] > 0  # correction columns in both kernels
     ref = None
     for cfg in CONFIGS:
         raw, k, V, resolved = _run(model, m, spec, cfg, steps)
@@ -71,7 +78,7 @@ def test_every_launch_config_gives_the_same_words(case):
             # at the threshold the two may stop one iteration apart
             assert abs(k - ok) <= (1 if case == "infinite" else 0)
             tol = TOL_F64 * max(1.0, float(np.max(np.abs(oV))))
-            if case == "f32":
+            if case.startswith("f32"):
                 tol = K * model.error_bound() + TOL_F64
             if case == "infinite":
                 tol = 1e-7
@@ -123,3 +130,41 @@ def test_autotune_picks_a_config_and_caches_it(tmp_path):
     assert ms2 == 0.0 and cfg2 == cfg
     sess2.close()
     assert os.path.exists(cache)
+
+
+@pytest.mark.parametrize("cfg", [dict(kernel=g.KERNEL_RING), dict(kernel=g.KERNEL_DIRECT, tile_entries=512)])
+def test_finished_problems_leave_the_tile_walk(cfg):
+    # Problems of different horizons (the longest not first) and one infinite
+    # horizon in one session: launches walk only the running problems' tiles.
+    # Every result equals the problem run alone, to the bit, and a restore into
+    # the finished session brings a problem's tiles back.
+    ms = [banded_imdp(200 + 30 * i, 1 + i % 2, (200 + 30 * i) * (1 + i % 2) * 12 + 1, seed=90 + i) for i in range(5)]
+    models = [g.create_model(x) for x in ms]
+    horizons = [7, 40, 3, 25, None]
+    specs = [g.make_spec(horizon=h, reach=x.goal) if h else
+             g.make_spec(infinite_time=True, eps=1e-9, horizon=100000, reach=x.goal) for x, h in zip(ms, horizons)]
+    sess = g.imdp_session_create(models, specs)
+    g.imdp_session_set_launch(sess, **cfg)
+    g.imdp_session_run(sess)
+    for i, (x, sp) in enumerate(zip(ms, specs)):
+        raw, k = g.imdp_session_checkpoint(sess, i)
+        alone = g.imdp_session_create([models[i]], [sp])
+        g.imdp_session_set_launch(alone, **cfg)
+        g.imdp_session_run(alone)
+        raw1, k1 = g.imdp_session_checkpoint(alone, 0)
+        alone.close()
+        assert k == k1 and np.array_equal(raw, raw1), i
+    # every problem is done: restore problem 1 to iteration 10 and run again
+    raw_full, k_full = g.imdp_session_checkpoint(sess, 1)
+    first = g.imdp_session_create([models[1]], [specs[1]])
+    g.imdp_session_step(first, 10)
+    raw10, k10 = g.imdp_session_checkpoint(first, 0)
+    first.close()
+    g.imdp_session_restore(sess, 1, raw10, k10)
+    g.imdp_session_run(sess)
+    V, kk = np.zeros(ms[1].n_states), [0]
+    g.imdp_session_read(sess, 1, V, kk)
+    assert kk[0] == 40
+    _, oV, _, _, _ = run_oracle(ms[1], horizon=40, reach=ms[1].goal)
+    np.testing.assert_allclose(V, oV, rtol=0, atol=TOL_F64)
+    sess.close()

@@ -24,6 +24,11 @@ def _lockstep(m, parts, spec_kw, dtype=g.IMDP_F64):
         owns = [r.step().clone() for r in runners]
         for r in runners:
             r.put(owns)
+        if runners[0].infinite:
+            # the maximum of the slices' residuals decides, for every slice
+            rmax = max(int(r.residual().item()) for r in runners)
+            if rmax < runners[0].eps_raw:
+                break
     out = []
     for r in runners:
         V = np.zeros(m.n_states)
@@ -75,13 +80,43 @@ def test_sharded_reach_avoid_reward_and_f32():
     np.testing.assert_array_equal(outs[0][0], Vw)
 
 
+@pytest.mark.parametrize("parts", [2, 3])
+def test_sharded_infinite_horizon_equals_whole(parts):
+    # the slices stop on the maximum residual over all of them: the same
+    # iteration count and the same words as the unsharded infinite run
+    m = banded_imdp(500, 2, 500 * 2 * 20 + 1, eps=0.05, seed=85)
+    for kw in (dict(infinite_time=True, eps=1e-8, horizon=100000, reach=m.goal),
+               dict(infinite_time=True, eps=1e-6, horizon=100000, reach=m.goal, pessimistic=False, maximize=False)):
+        Vw, kw_ = _whole(m, kw)
+        b, outs = _lockstep(m, parts, kw)
+        for V, k in outs:
+            assert k == kw_ > 10
+            np.testing.assert_array_equal(V, Vw)
+    r = np.linspace(0.0, 1.0, m.n_states)
+    kw = dict(property=g.IMDP_REWARD, infinite_time=True, eps=1e-7, horizon=100000, reward=r, discount=0.9)
+    Vw, kw_ = _whole(m, kw)
+    _, outs = _lockstep(m, 2, kw)
+    assert outs[0][1] == kw_
+    np.testing.assert_array_equal(outs[0][0], Vw)
+
+
 def test_slice_errors():
     m = banded_imdp(100, 1, 100 * 10 + 1, seed=84)
     sm = g.create_model_slice(m, 0, 50)
-    # an infinite horizon would test convergence on the owned states only
+    # an infinite horizon on a slice stops on the residual of all slices: the
+    # session may be stepped, but not run to convergence on its own states
+    s_inf = g.imdp_session_create([sm], [g.make_spec(infinite_time=True, eps=1e-6, reach=m.goal)])
     with pytest.raises(g.ImdpError) as e:
-        g.imdp_session_create([sm], [g.make_spec(infinite_time=True, eps=1e-6, reach=m.goal)])
+        g.imdp_session_run(s_inf)
     assert e.value.status == g.IMDP_EINVAL
+    with pytest.raises(g.ImdpError):
+        g.value_iteration(sm, m.n_states, infinite_time=True, eps=1e-6, reach=m.goal)
+    g.imdp_session_step(s_inf, 2)
+    res = torch.zeros(1, dtype=torch.int64, device="cuda")
+    g.imdp_session_residual(s_inf, 0, 2, 0, 50, res)
+    with pytest.raises(g.ImdpError):
+        g.imdp_session_residual(s_inf, 0, 0, 0, 50, res)  # k >= 1
+    s_inf.close()
     # slices run in sessions only
     srv = g.imdp_server_create(16 << 20)
     with pytest.raises(g.ImdpError):

@@ -391,6 +391,10 @@ CONFIGS = {
     "harrier": dict(kind="single", n_domain=25920, n_actions=1, nnz=18574307, eps=0.05, seed=5),
     # pimdp_2: 42634 states, 3 actions, 48106480 transitions (the paper's largest model)
     "pimdp2": dict(kind="single", n_domain=42633, n_actions=3, nnz=48106480, eps=0.05, seed=6),
+    # dense: every column lists every grid state (plus the sink), as a dense
+    # IntervalProbabilities matrix of Sec. 3.1 would; 4096 states, 2 actions
+    "dense4096": dict(kind="single", n_domain=4095, n_actions=2, nnz=4095 * 2 * 4095 + 4095 * 2 + 1, eps=0.05,
+                      seed=8),
 }
 
 
