@@ -124,12 +124,24 @@ def reduce_across_ranks(elapsed_ms: float, kernel_ms: float, units: float, world
     return float(mx[0]), float(mx[1]), float(sm[0])
 
 
-def algorithmic_bytes_per_iteration(m, storage: str = "f64") -> int:
-    """rowval + lower + gap per transition; colptr + rem (+ shift) per column;
-    stateptr + V read + V write per state."""
+def algorithmic_bytes_per_iteration(m, storage: str = "f64", exact_entries: int = 0, fixed=None) -> int:
+    """rowval + lower + gap per transition; colptr + rem (+ shift and the
+    correction offset) per column; stateptr + V read + V write per state. On
+    32-bit storage a correction column's transitions keep 4 + 16 bytes. States
+    in ``fixed`` (the reach / avoid targets, whose values Eq. 2 fixes) are
+    read and written by no launch and are left out."""
+    nnz, ncols, nst = int(m.nnz), int(m.n_cols), int(m.n_states)
+    if fixed is not None and len(fixed):
+        f = np.unique(np.asarray(fixed, np.int64))
+        cols = np.asarray(m.stateptr, np.int64)
+        ent = np.asarray(m.colptr, np.int64)
+        nnz -= int((ent[cols[f + 1]] - ent[cols[f]]).sum())
+        ncols -= int((cols[f + 1] - cols[f]).sum())
+        nst -= int(f.size)
     if storage == "f32":
-        return 12 * int(m.nnz) + 16 * int(m.n_cols) + 20 * int(m.n_states)
-    return 20 * int(m.nnz) + 12 * int(m.n_cols) + 20 * int(m.n_states)
+        return (12 * (nnz - exact_entries) + 20 * exact_entries + (20 if exact_entries else 16) * ncols
+                + 20 * nst)
+    return 20 * nnz + 12 * ncols + 20 * nst
 
 
 def bellman_source_hash() -> str:
@@ -248,7 +260,7 @@ def run_ours(args, rank, world, local_rank):
 
     m = make_workload(args.workload, rank, args.models)
     dtype = g.IMDP_F32 if args.dtype == "f32" else g.IMDP_F64
-    model = g.create_model(m, dtype=dtype, stream=stream)
+    model = g.create_model(m, dtype=dtype, stream=stream, budget=f32_budget(args))
     if args.infinite:
         spec = g.make_spec(infinite_time=True, eps=args.eps, horizon=1000000, reach=m.goal, pessimistic=True,
                            maximize=True)
@@ -335,7 +347,8 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return
     peak, peak_kind = measured_peak_hbm()
-    alg_bytes = algorithmic_bytes_per_iteration(m, args.dtype)
+    # correction entries of the fixed states are not read either; counting them is a slight overestimate
+    alg_bytes = algorithmic_bytes_per_iteration(m, args.dtype, g.imdp_model_exact_columns(model)[1], fixed=m.goal)
     launch_ms = kernel_ms / max(1, launches)  # per launched iteration (includes any past convergence)
     n_tiles, n_wide, wide_entries = g.imdp_session_plan(sess)
     wide_share = wide_entries / max(1, m.nnz)
@@ -354,12 +367,15 @@ def run_ours(args, rank, world, local_rank):
         cfg["query"] = "maximize pessimistic reachability, infinite horizon"
     if args.policy:
         cfg["policy"] = "time-dependent, K x n int32 written every iteration"
-    cfg["storage"] = "32-bit bounds (per-column scaled), 64-bit arithmetic" if args.dtype == "f32" else \
-        "64-bit bounds (Q1.63), 64-bit arithmetic"
+    cfg["storage"] = ("32-bit bounds (per-column scaled) and values, 32-bit arithmetic; correction columns exact"
+                      if args.dtype == "f32" else "64-bit bounds (Q1.63), 64-bit arithmetic")
     cfg["launch"] = launch
     if args.dtype == "f32":
-        cfg["error_bound_per_iteration"] = model.error_bound()
-        cfg["error_bound_horizon"] = model.error_bound() * args.horizon
+        n_exact, exact_entries, budget = g.imdp_model_exact_columns(model)
+        cfg["error_bound_per_iteration"] = model.error_bound()  # guaranteed
+        cfg["error_bound_horizon"] = model.error_bound() * iters
+        cfg["correction_columns"] = {"columns": n_exact, "transitions": exact_entries,
+                                     "share_of_transitions": exact_entries / max(1, m.nnz), "budget": budget}
     out = {
         "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -386,6 +402,11 @@ def run_ours(args, rank, world, local_rank):
 
 
 TUNE_CACHE = os.path.join(ROOT, "paper_2401_04068_gb300", "tuned_gb300.json")
+
+
+def f32_budget(args):
+    """Per-iteration error budget of 32-bit storage (None: the library's default)."""
+    return args.f32_budget if (args.dtype == "f32" and args.f32_budget > 0) else None
 
 
 def parse_launch(text: str) -> dict:
@@ -448,7 +469,7 @@ def run_uneven(args, rank, world, local_rank):
     ms, Ks = uneven_batch(n, seed=7 + 1000 * rank, threads=os.cpu_count() or 1)
     gen_s = time.perf_counter() - t
     dtype = g.IMDP_F32 if args.dtype == "f32" else g.IMDP_F64
-    models = [g.create_model(m, dtype=dtype, stream=stream) for m in ms]
+    models = [g.create_model(m, dtype=dtype, stream=stream, budget=f32_budget(args)) for m in ms]
     specs = [g.make_spec(horizon=int(K), reach=m.goal, pessimistic=True, maximize=True) for m, K in zip(ms, Ks)]
     sess = g.imdp_session_create(models, specs, stream=stream)
     kmax = int(Ks.max())
@@ -495,7 +516,8 @@ def run_uneven(args, rank, world, local_rank):
     if rank != 0:
         return
     peak, peak_kind = measured_peak_hbm()
-    alg = sum(algorithmic_bytes_per_iteration(m, args.dtype) * int(K) for m, K in zip(ms, Ks))
+    alg = sum(algorithmic_bytes_per_iteration(m, args.dtype, g.imdp_model_exact_columns(x)[1], fixed=m.goal)
+              * int(K) for m, x, K in zip(ms, models, Ks))
     achieved = alg * args.steps / (kernel_ms / 1e3) / 1e9
     out = {
         "metric": METRIC.replace("K=200", "K per problem"), "value": total_units / (elapsed_ms / 1e3), "unit": UNIT,
@@ -528,23 +550,29 @@ def run_latency(args, rank, world, local_rank):
     dev = _gpu_setup(rank, world, local_rank)
     stream = torch.cuda.Stream(device=dev)
     if args.workload == "worked_example":
+        # the Sec. 3.1 model as the paper states it: dense interval matrices per
+        # source state (rows = destinations, columns = actions), through the
+        # dense creation call
         ex = json.load(open(os.path.join(ROOT, "tests", "golden", "worked_example.json")))
-
-        class _M:
-            pass
-        m = _M()
-        m.n_states = ex["n_states"]
-        for k in ("stateptr", "colptr", "rowval"):
-            setattr(m, k, np.asarray(ex[k], np.int32))
-        m.lower = np.asarray(ex["lower"], np.float64)
-        m.upper = np.asarray(ex["upper"], np.float64)
-        m.goal = np.asarray(ex["goal"], np.int32)
-        K = 100
+        n = ex["n_states"]
+        n_actions = np.array([len(a) for a in ex["actions"]], np.int32)
+        lo = np.array([col for s in range(n) for col in ex["lower"][s]], np.float64).T.copy(order="F")
+        up = np.array([col for s in range(n) for col in ex["upper"][s]], np.float64).T.copy(order="F")
+        model = g.imdp_create_dense(n, n_actions, lo.ravel(order="F"), up.ravel(order="F"), stream=stream)
+        info = model.info()
+        n_states, ncols, nnz = info["n_states"], info["n_cols"], info["nnz"]
+        goal = np.array([x - 1 for x in ex["goal_1based"]], np.int32)
+        K = ex["horizon"]
     else:
         m = make_config("linear5")
         K = 200
-    nnz, ncols = len(m.rowval), len(m.colptr) - 1
-    model = g.create_model(m, stream=stream)
+        n_states, ncols, nnz, goal = m.n_states, len(m.colptr) - 1, len(m.rowval), m.goal
+        model = g.create_model(m, stream=stream)
+
+    class _M:  # what the rest of the function reads
+        pass
+    m = _M()
+    m.n_states, m.goal = n_states, goal
     spec = g.make_spec(horizon=K, reach=m.goal)
     Vh = torch.empty(m.n_states, dtype=torch.float64).pin_memory()
     kk = [0]
@@ -627,6 +655,11 @@ def run_served(args, rank, world, local_rank):
     n_req = args.requests
     models_h, reqs = served_stream(n_req, seed=8 + 1000 * rank, threads=os.cpu_count() or 1)
     server = g.imdp_server_create(int(args.server_budget_gb * (1 << 30)))
+    launch = {"kernel": 0, "chosen_by": "rule"}
+    if args.launch:
+        launch = parse_launch(args.launch)
+        g.imdp_server_set_launch(server, **launch)
+        launch["chosen_by"] = "explicit"
     # warm-up: one request through the whole path (module load, first graph)
     w = g.create_model(models_h[0], stream=stream)
     tk = g.imdp_server_submit(server, w, g.make_spec(horizon=10, reach=models_h[0].goal))
@@ -715,6 +748,7 @@ def run_served(args, rank, world, local_rank):
         "ms_per_step": span * 1e3 / n_req, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic (seeded banded IMDPs, log-uniform shapes)",
         "config": {"workload": f"served_poisson{int(args.rate)}", "requests": n_req, "rate_per_s": args.rate,
+                   "launch": launch,
                    "new_models": len(models_h), "client_threads": args.client_threads,
                    "shapes": "states log-U[50,4000], actions U{1..3}, "
                    "window log-U[3,700], K U{100..500}", "server_budget_gb": args.server_budget_gb,
@@ -802,6 +836,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="storage of the transition bounds")
+    ap.add_argument("--f32-budget", type=float, default=0.0,
+                    help="32-bit storage: per-iteration error budget of the correction stage (0: library default)")
     ap.add_argument("--launch", default="", help="explicit launch configuration, e.g. ring:24 or direct:4:1024")
     ap.add_argument("--tune", default="cache", choices=["cache", "fresh", "off"],
                     help="autotuner: cached choice (timing only shapes missing from the cache), time now, or rule")

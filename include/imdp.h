@@ -422,6 +422,11 @@ IMDP_API imdp_status imdp_session_restore(imdp_session* s, int32_t index, const 
  */
 typedef struct imdp_server imdp_server;
 IMDP_API imdp_status imdp_server_create(size_t hbm_budget, imdp_server** out);
+/* Launch configuration of the server's Bellman launches (imdp_launch_config;
+ * zero fields by rule). Requests admitted afterwards are planned with its tile
+ * limits; it may change while requests run (a running request keeps its plan).
+ * Thread-safe. IMDP_EINVAL for NULL or a bad configuration. */
+IMDP_API imdp_status imdp_server_set_launch(imdp_server* s, const imdp_launch_config* cfg);
 /* Queue a request; returns at once with a ticket. IMDP_ENOMEM if the request
  * alone exceeds the budget, IMDP_EBUSY if the queue is full. */
 IMDP_API imdp_status imdp_server_submit(imdp_server* s, imdp_model* m, const imdp_spec* spec, uint64_t* ticket);

@@ -35,6 +35,7 @@ EXPORTED = [
     "imdp_session_checkpoint", "imdp_session_restore",
     "imdp_session_set_launch", "imdp_session_get_launch", "imdp_session_autotune", "imdp_session_plan",
     "imdp_create_csc_f32", "imdp_model_exact_columns", "imdp_session_residual", "imdp_session_stop_threshold",
+    "imdp_server_set_launch",
 ]
 
 
@@ -131,6 +132,7 @@ def load(path: Optional[str] = None):
     lib.imdp_session_set_launch.argtypes = [vp, C.POINTER(imdp_launch_config), vp]
     lib.imdp_session_get_launch.argtypes = [vp, C.POINTER(imdp_launch_config)]
     lib.imdp_session_plan.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
+    lib.imdp_server_set_launch.argtypes = [vp, C.POINTER(imdp_launch_config)]
     lib.imdp_session_residual.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, vp]
     lib.imdp_session_stop_threshold.argtypes = [vp, C.c_int32, C.POINTER(C.c_uint64)]
     lib.imdp_session_autotune.argtypes = [vp, C.c_int32, C.c_char_p, vp, C.POINTER(imdp_launch_config),
@@ -497,6 +499,13 @@ def imdp_server_create(hbm_budget: int) -> Server:
     out = C.c_void_p()
     _check(load().imdp_server_create(int(hbm_budget), C.byref(out)), "imdp_server_create")
     return Server(out.value)
+
+
+def imdp_server_set_launch(server: Server, kernel: int = 0, cta_warps: int = 0, ctas_per_sm: int = 0,
+                           tile_entries: int = 0, wide_col: int = 0):
+    """Launch configuration of the server's Bellman launches (0 fields: by rule)."""
+    cfg = imdp_launch_config(kernel, cta_warps, ctas_per_sm, tile_entries, wide_col)
+    _check(load().imdp_server_set_launch(C.c_void_p(server.handle), C.byref(cfg)), "imdp_server_set_launch")
 
 
 def imdp_server_submit(server: Server, model: Model, spec) -> int:

@@ -149,6 +149,17 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t 
       : "memory");
   return ok != 0;
 }
+// try_wait with a suspend-time hint: the thread sleeps in hardware until the
+// phase completes or about `ns` nanoseconds pass, instead of spinning.
+__device__ __forceinline__ bool mbar_try_wait_sleep(unsigned long long* bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
@@ -161,9 +172,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 __device__ bool wait_phase(unsigned long long* bar, uint32_t parity, unsigned* err, bool drain) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (!drain && *(volatile unsigned*)err) return false;
+  for (uint32_t i = 0;; ++i) {
+    // each try sleeps up to ~20 us unless the phase completes first; the error
+    // word (another CTA gave up) and the clock are checked between tries
+    if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+    if (!drain && (i & 7) == 7 && *(volatile unsigned*)err) return false;
     if (clock64() - t0 > kWaitCycles) {
       atomicExch(err, 1u);
       return false;
@@ -368,6 +381,116 @@ __device__ __forceinline__ uint64_t mul_shr(uint64_t a, uint64_t b, int s) {
 // x << d, saturating at 2^64 - 1.
 __device__ __forceinline__ uint64_t shl_sat(uint64_t x, int d) { return (x >> (64 - d)) ? ~0ull : x << d; }
 
+// Per-warp streaming ring of the direct kernel's warm pass: every lane copies
+// its own entries (destination and bound pair) of trips t + 1 .. t + kRingDepth
+// into shared memory with cp.async while trip t is computed, so that a warp
+// keeps kRingDepth trips of loads in flight without holding them in
+// registers. Entries past the column's end are zero-filled by the copy (source
+// size 0: nothing is read), which is what the warm pass's padding lanes use.
+constexpr int kRingDepth = 4;
+constexpr int kRingSlots = kRingDepth + 1;  // the slot being refilled is never the one being read
+struct StreamRing {
+  int32_t rows[kRingSlots][32];
+  ulonglong2 lg[kRingSlots][32];  // 32-bit storage uses the first half of each slot as uint2[32]
+};
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(ok ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(ok ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(ok ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Copies of trip t (this lane's entry) into its ring slot, then one commit
+// (an empty group past the last trip, so that every trip is one group).
+template <bool f32>
+__device__ __forceinline__ void ring_issue(StreamRing* R, int slot, const int32_t* rows, const void* lg, int t,
+                                           int nb, int32_t k, int lane) {
+  if (t < nb) {
+    const int idx = t * 32 + lane;
+    const bool ok = idx < k;
+    const int i = ok ? idx : 0;
+    cp_async4(&R->rows[slot][lane], rows + i, ok);
+    if (f32)
+      cp_async8(reinterpret_cast<uint2*>(&R->lg[slot][0]) + lane, static_cast<const uint2*>(lg) + i, ok);
+    else
+      cp_async16(&R->lg[slot][lane], static_cast<const ulonglong2*>(lg) + i, ok);
+  }
+  cp_async_commit();
+}
+
+// warm_pass (64-bit storage) over a column in global memory, fed by the ring.
+template <bool carry>
+__device__ __forceinline__ void warm_pass_ring(const int32_t* rows, const ulonglong2* lg, int32_t k,
+                                               const uint64_t* __restrict__ V, uint64_t vk, bool pess, int lane,
+                                               uint64_t& acc, uint64_t& flt, uint64_t& geq, StreamRing* R) {
+  uint32_t fc = 0, gc = 0;
+  const int nb = (k + 31) >> 5;
+#pragma unroll
+  for (int t = 0; t < kRingDepth; ++t) ring_issue<false>(R, t, rows, lg, t, nb, k, lane);
+  int slot = 0, fill = kRingDepth;
+  for (int it = 0; it < nb; ++it) {
+    cp_async_wait<kRingDepth - 1>();  // trip `it` has landed
+    const int32_t r = R->rows[slot][lane];
+    const ulonglong2 b = R->lg[slot][lane];
+    ring_issue<false>(R, fill, rows, lg, it + kRingDepth, nb, k, lane);
+    slot = slot + 1 == kRingSlots ? 0 : slot + 1;
+    fill = fill + 1 == kRingSlots ? 0 : fill + 1;
+    const uint64_t v = ld_value(V + r);
+    const bool below = pess ? (v < vk) : (v > vk);
+    acc += __umul64hi(v, b.x + (below ? b.y : 0ull));
+    const uint64_t gb = below ? b.y : 0ull, ge = v == vk ? b.y : 0ull;
+    flt += gb;
+    geq += ge;
+    if (carry) {
+      fc += flt < gb ? 1u : 0u;
+      gc += geq < ge ? 1u : 0u;
+    }
+  }
+  cp_async_wait<0>();
+  if (carry) {
+    flt = fc ? ~0ull : flt;
+    geq = gc ? ~0ull : geq;
+  }
+}
+
+// warm_pass32 over a column in global memory, fed by the ring.
+__device__ __forceinline__ void warm_pass32_ring(const int32_t* rows, const uint2* m, int32_t k,
+                                                 const uint64_t* __restrict__ V, uint32_t vk, int s, bool pess,
+                                                 int lane, uint64_t& acc, uint64_t& flt, uint64_t& geq,
+                                                 StreamRing* R) {
+  const int nb = (k + 31) >> 5;
+#pragma unroll
+  for (int t = 0; t < kRingDepth; ++t) ring_issue<true>(R, t, rows, m, t, nb, k, lane);
+  int slot = 0, fill = kRingDepth;
+  for (int it = 0; it < nb; ++it) {
+    cp_async_wait<kRingDepth - 1>();
+    const int32_t r = R->rows[slot][lane];
+    const uint2 b = reinterpret_cast<const uint2*>(&R->lg[slot][0])[lane];
+    ring_issue<true>(R, fill, rows, m, it + kRingDepth, nb, k, lane);
+    slot = slot + 1 == kRingSlots ? 0 : slot + 1;
+    fill = fill + 1 == kRingSlots ? 0 : fill + 1;
+    const uint32_t v = ld_value_hi(V + r);
+    const bool below = pess ? (v < vk) : (v > vk);
+    const uint32_t g = below ? b.y : 0u;
+    acc += ((uint64_t)v * (uint64_t)(b.x + g)) >> s;
+    flt += g;
+    geq += v == vk ? b.y : 0u;
+  }
+  cp_async_wait<0>();
+}
+
 // `rem_word` is rem = 1 - sum(lower) in Q1.63 (<= 2^63); when 0 < rem < 2^63 and
 // the column's gaps add up to < 2^64 ("narrow"), model creation sets bit 63 as a
 // flag on top of rem.
@@ -392,7 +515,7 @@ struct WarmMiss {
 template <bool f32, bool gmem>
 __device__ __forceinline__ bool column_warm(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem_word,
                                             const uint64_t* __restrict__ V, bool pess, int lane, int32_t hint,
-                                            uint64_t* q, WarmMiss* miss) {
+                                            uint64_t* q, WarmMiss* miss, StreamRing* ring = nullptr) {
   miss->valid = false;
   const uint64_t rem = rem_of(rem_word);
   if (rem == 0) {
@@ -408,7 +531,14 @@ __device__ __forceinline__ bool column_warm(const typename RowsOf<gmem>::type ro
     const int down = lg.down, sh = 32 - down;
     const uint32_t vk32 = ld_value_hi(V + rows[hint]);
     uint64_t acc = 0, flt = 0, geq = 0;
-    warm_pass32<gmem>(rows, static_cast<const uint2*>(lg.p), k, V, vk32, sh, pess, lane, acc, flt, geq);
+    if constexpr (gmem) {
+      if (ring)
+        warm_pass32_ring(rows.p, static_cast<const uint2*>(lg.p), k, V, vk32, sh, pess, lane, acc, flt, geq, ring);
+      else
+        warm_pass32<gmem>(rows, static_cast<const uint2*>(lg.p), k, V, vk32, sh, pess, lane, acc, flt, geq);
+    } else {
+      warm_pass32<gmem>(rows, static_cast<const uint2*>(lg.p), k, V, vk32, sh, pess, lane, acc, flt, geq);
+    }
     acc = warp_sum_u64(acc);
     flt = warp_sum_u64(flt);
     geq = warp_sum_u64(geq);
@@ -422,7 +552,25 @@ __device__ __forceinline__ bool column_warm(const typename RowsOf<gmem>::type ro
   }
   const uint64_t vk = ld_value(V + rows[hint]);
   uint64_t acc = 0, flt = 0, geq = 0;
-  if (narrow_of(rem_word)) {
+  bool streamed = false;
+  if constexpr (gmem && !f32) {
+    if (ring) {  // the direct kernel: loads in flight through the ring
+      if (narrow_of(rem_word))
+        warm_pass_ring<false>(rows.p, static_cast<const ulonglong2*>(lg.p), k, V, vk, pess, lane, acc, flt, geq, ring);
+      else
+        warm_pass_ring<true>(rows.p, static_cast<const ulonglong2*>(lg.p), k, V, vk, pess, lane, acc, flt, geq, ring);
+      streamed = true;
+    }
+  }
+  if (streamed) {
+    if (narrow_of(rem_word)) {
+      flt = warp_sum_u64(flt);
+      geq = warp_sum_u64(geq);
+    } else {
+      flt = warp_sum_sat(flt);
+      geq = warp_sum_sat(geq);
+    }
+  } else if (narrow_of(rem_word)) {
     // every gap sum of a narrow column is below 2^64: plain exact sums
     warm_pass<false, f32, gmem>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
     flt = warp_sum_u64(flt);
@@ -685,7 +833,7 @@ __device__ uint64_t column_search(const typename RowsOf<gmem>::type rows, const 
 template <bool f32, bool gmem>
 __device__ uint64_t column_q(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem_word,
                              const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane, int32_t hint,
-                             int32_t* hint_out) {
+                             int32_t* hint_out, StreamRing* ring = nullptr) {
   // A hint of -2 - i names entry i as well and records that the column's last
   // value came from the full search: its threshold is moving fast, so a miss
   // goes to the search without trying the neighbour.
@@ -693,7 +841,7 @@ __device__ uint64_t column_q(const typename RowsOf<gmem>::type rows, const Bound
   const int32_t entry = moving ? -2 - hint : hint;
   uint64_t q;
   WarmMiss miss;
-  if (column_warm<f32, gmem>(rows, lg, k, rem_word, V, pess, lane, entry, &q, &miss)) {
+  if (column_warm<f32, gmem>(rows, lg, k, rem_word, V, pess, lane, entry, &q, &miss, ring)) {
     *hint_out = entry;
     return q;
   }
@@ -807,14 +955,17 @@ __device__ __forceinline__ void stage_column(Stage& st, const Tile& T, int32_t l
   const int32_t ca = st.cptr[c - cb], ce = st.cptr[c + 1 - cb];
   const int32_t h = P.hint ? st.hint[c - cb] : -1;
   if (f32 && P.xoff) {
-    // a correction column of 32-bit storage: its exact bounds are not staged,
-    // so it reads them (and its destinations) from global memory
+    // a correction column of 32-bit storage: its exact pairs are staged after
+    // the tile's mantissa pairs (at its offset within the tile's range of lgx)
     const int32_t xo = __ldg(P.xoff + c);
     if (xo >= 0) {
+      const int32_t qb = T.e0 & ~1, qe = (T.e1 + 1) & ~1;
+      const ulonglong2* xs = reinterpret_cast<const ulonglong2*>(reinterpret_cast<const unsigned char*>(st.lg) +
+                                                                  (size_t)(qe - qb) * 8u);
       int32_t hout;
-      const uint64_t q = column_q<false, true>(GRows{P.rowval + ca}, Bounds<false, true>{P.lgx + xo, 0}, ce - ca,
-                                               st.rem[c - mb], P.V[(k_iter - 1) & 1], P.pessimistic != 0, ws, lane,
-                                               h, &hout);
+      const uint64_t q = column_q<false, false>(st.rows + (ca - eb), Bounds<false>{xs + (xo - T.x0), 0}, ce - ca,
+                                                st.rem[c - mb], P.V[(k_iter - 1) & 1], P.pessimistic != 0, ws, lane,
+                                                h, &hout);
       if (lane == 0) {
         st.q[li] = q;
         if (P.hint && hout != h) P.hint[c] = hout;
@@ -899,7 +1050,9 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) bellman_step_kernel(StepLaunc
           // bounds: 16-byte pairs, or (32-bit storage) 8-byte pairs from an aligned
           // window plus the per-column shift window
           const int32_t qb = T.e0 & ~1, qe = (T.e1 + 1) & ~1;
-          const uint32_t gb = P.lg32 ? (uint32_t)(qe - qb) * 8u + (uint32_t)(((T.c1 + 4) & ~3) - (T.c0 & ~3)) * 4u
+          const uint32_t xbytes = P.lg32 ? (uint32_t)(T.x1 - T.x0) * 16u : 0u;
+          const uint32_t gb = P.lg32 ? (uint32_t)(qe - qb) * 8u + (uint32_t)(((T.c1 + 4) & ~3) - (T.c0 & ~3)) * 4u +
+                                           xbytes
                                      : (uint32_t)(T.e1 - T.e0) * 16u;
           const uint32_t sbytes = (uint32_t)(se - sb) * 4u, cbytes = (uint32_t)(ce - cb) * 4u;
           const uint32_t mbytes = (uint32_t)(me - mb) * 8u, fbytes = (uint32_t)(fe - fa);
@@ -917,6 +1070,9 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) bellman_step_kernel(StepLaunc
             const uint32_t qbytes = (uint32_t)(qe - qb) * 8u;
             if (qbytes) bulk_g2s(st.lg, P.lg32 + qb, qbytes, &S.full[stage]);
             bulk_g2s(st.shift, P.shift + cb, cbytes, &S.full[stage]);
+            // the correction columns' exact pairs, after the mantissas (the
+            // planner keeps both within the bound area)
+            if (xbytes) bulk_g2s(reinterpret_cast<unsigned char*>(st.lg) + qbytes, P.lgx + T.x0, xbytes, &S.full[stage]);
           } else if (gb) {
             bulk_g2s(st.lg, P.lg + T.e0, gb, &S.full[stage]);
           }
@@ -1092,7 +1248,8 @@ struct ColChunk {
 };
 
 template <bool f32>
-__device__ void direct_tile(const StepLaunch& L, const Tile& T, int32_t k_iter, WarpScratch* ws, int lane) {
+__device__ void direct_tile(const StepLaunch& L, const Tile& T, int32_t k_iter, WarpScratch* ws, StreamRing* ring,
+                            int lane) {
   const Problem& P = L.probs[T.p];
   const uint64_t* __restrict__ Vin = P.V[(k_iter - 1) & 1];
   uint64_t* __restrict__ Vout = P.V[k_iter & 1];
@@ -1159,13 +1316,13 @@ __device__ void direct_tile(const StepLaunch& L, const Tile& T, int32_t k_iter, 
           if (f32 && xo < 0)
             q = column_q<true, true>(GRows{P.rowval + ca},
                                      Bounds<true, true>{P.lg32 + ca, 32 - __shfl_sync(kFull, cc.shift, src)}, ce - ca,
-                                     rw, Vin, pess, ws, lane, h, &hout);
+                                     rw, Vin, pess, ws, lane, h, &hout, ring);
           else if (f32)  // correction column: its exact bounds
             q = column_q<false, true>(GRows{P.rowval + ca}, Bounds<false, true>{P.lgx + xo, 0}, ce - ca, rw, Vin,
-                                      pess, ws, lane, h, &hout);
+                                      pess, ws, lane, h, &hout, ring);
           else
             q = column_q<false, true>(GRows{P.rowval + ca}, Bounds<false, true>{P.lg + ca, 0}, ce - ca, rw, Vin, pess,
-                                      ws, lane, h, &hout);
+                                      ws, lane, h, &hout, ring);
           if (lane == 0 && hint && hout != h) hint[c] = hout;
           if (best < 0 || (maxi ? q > bq : q < bq)) {
             bq = q;
@@ -1183,6 +1340,7 @@ __device__ void direct_tile(const StepLaunch& L, const Tile& T, int32_t k_iter, 
 template <int NW, int MINB>
 __global__ void __launch_bounds__(32 * NW, MINB) bellman_direct_kernel(StepLaunch L) {
   __shared__ WarpScratch ws_all[NW];
+  __shared__ StreamRing rings[NW];
   __shared__ int is_last;
   const int lane = threadIdx.x & 31;
   WarpScratch* ws = &ws_all[threadIdx.x >> 5];
@@ -1196,9 +1354,9 @@ __global__ void __launch_bounds__(32 * NW, MINB) bellman_direct_kernel(StepLaunc
     int32_t k_iter;
     if (!problem_active(L, T.p, &k_iter)) continue;
     if (L.probs[T.p].lg32)
-      direct_tile<true>(L, T, k_iter, ws, lane);
+      direct_tile<true>(L, T, k_iter, ws, &rings[threadIdx.x >> 5], lane);
     else
-      direct_tile<false>(L, T, k_iter, ws, lane);
+      direct_tile<false>(L, T, k_iter, ws, &rings[threadIdx.x >> 5], lane);
   }
   end_of_launch(L, &is_last);
 }
@@ -1654,20 +1812,39 @@ __global__ void __launch_bounds__(kWideThreads, 6) bellman_wide_kernel(StepLaunc
 }  // namespace
 
 void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out, std::vector<int32_t>& wide,
-                int32_t tile_entries, int32_t wide_col) {
+                int32_t tile_entries, int32_t wide_col, const uint8_t* fixed) {
   const std::vector<int32_t>& sp = m->h_stateptr;
   const std::vector<int32_t>& cp = m->h_colptr;
   const int32_t n = m->own1;  // owned states only
   const int32_t te = tile_entries > 0 && tile_entries < kTileEntries ? tile_entries : kTileEntries;
   const int32_t wc = wide_col > 0 ? wide_col : kWideCol;
+  // states whose values the property fixes (Eq. 2) are in no tile and no wide list
+  auto is_fixed = [&](int32_t s) { return fixed && fixed[s]; };
+  // 32-bit storage with correction columns: a stage's bound area holds the
+  // tile's 8-byte mantissa pairs followed by its correction columns' 16-byte
+  // exact pairs
+  const std::vector<int32_t>& xo = m->h_xoff;
+  auto stage_fits = [&](int32_t c0, int32_t c1, int32_t e0, int32_t e1) {
+    if (xo.empty()) return true;
+    int64_t x = 0;
+    for (int32_t c = c0; c < c1; ++c)
+      if (xo[c] >= 0) x += cp[c + 1] - cp[c];
+    const int64_t pairs32 = (((int64_t)e1 + 1) & ~1) - (e0 & ~1);
+    return 8 * pairs32 + 16 * x <= (int64_t)sizeof(ulonglong2) * kTileEntries;
+  };
   auto is_wide = [&](int32_t s) {
     if (cp[sp[s + 1]] - cp[sp[s]] > kTileEntries || sp[s + 1] - sp[s] > kTileCols) return true;
+    if (!stage_fits(sp[s], sp[s + 1], cp[sp[s]], cp[sp[s + 1]])) return true;
     for (int32_t c = sp[s]; c < sp[s + 1]; ++c)
       if (cp[c + 1] - cp[c] >= wc) return true;
     return false;
   };
   int32_t s = m->own0;
   while (s < n) {
+    if (is_fixed(s)) {
+      ++s;
+      continue;
+    }
     if (is_wide(s)) {
       wide.push_back(s);
       ++s;
@@ -1679,12 +1856,25 @@ void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out, std:
     T.c0 = sp[s];
     T.e0 = cp[sp[s]];
     int32_t t = s + 1;
-    while (t < n && !is_wide(t) && cp[sp[t + 1]] - T.e0 <= te && sp[t + 1] - T.c0 <= kTileCols &&
-           t + 1 - s <= kTileStates)
+    while (t < n && !is_fixed(t) && !is_wide(t) && cp[sp[t + 1]] - T.e0 <= te && sp[t + 1] - T.c0 <= kTileCols &&
+           t + 1 - s <= kTileStates && stage_fits(T.c0, sp[t + 1], T.e0, cp[sp[t + 1]]))
       ++t;
     T.s1 = t;
     T.c1 = sp[T.s1];
     T.e1 = cp[T.c1];
+    T.x0 = T.x1 = 0;
+    if (!xo.empty()) {  // the correction columns' entries are consecutive in lgx
+      int32_t a = -1, b = -1;
+      for (int32_t c = T.c0; c < T.c1; ++c)
+        if (xo[c] >= 0) {
+          if (a < 0) a = xo[c];
+          b = xo[c] + (cp[c + 1] - cp[c]);
+        }
+      if (a >= 0) {
+        T.x0 = a;
+        T.x1 = b;
+      }
+    }
     out.push_back(T);
     s = T.s1;
   }

@@ -48,6 +48,7 @@ struct Tile {
   int32_t s0, s1; // states [s0, s1) of that problem
   int32_t c0, c1; // columns [c0, c1)
   int32_t e0, e1; // entries [e0, e1)
+  int32_t x0, x1; // 32-bit storage: the tile's correction entries, [x0, x1) of the model's lgx
 };
 
 // Device-resident model (the "IntervalMDP.cu(problem)" transfer of Sec. 3.2,
@@ -77,6 +78,7 @@ struct DevModel {
   size_t bytes = 0;
   std::vector<int32_t> h_stateptr;  // host copies of the structure (tile planning)
   std::vector<int32_t> h_colptr;
+  std::vector<int32_t> h_xoff;      // IMDP_F32 with correction columns: host copy of xoff
   std::vector<Tile> h_tiles;        // tile plan of this model (problem index 0)
   Tile* tiles = nullptr;            // device copy of h_tiles
   int32_t n_tiles = 0;
@@ -212,9 +214,10 @@ LaunchConfig resolve_launch(const StepLaunch& L, const LaunchConfig* cfg);
 // Tile plan for one problem's model (host): tiles appended to `out`, wide
 // states (no tile) appended to `wide`. Tiles hold at most `tile_entries`
 // entries (<= kTileEntries; 0: kTileEntries); a state with a column of
-// `wide_col` entries or more (0: kWideCol) is wide.
+// `wide_col` entries or more (0: kWideCol) is wide. States with a nonzero
+// `fixed` entry (nullable; n_states of the problem) belong to neither.
 void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out, std::vector<int32_t>& wide,
-                int32_t tile_entries = 0, int32_t wide_col = 0);
+                int32_t tile_entries = 0, int32_t wide_col = 0, const uint8_t* fixed = nullptr);
 
 // model.cu
 // Per-iteration error budget of 32-bit storage when the caller names none:
@@ -243,6 +246,7 @@ struct Session {
   std::vector<int32_t> base_h;
   std::vector<int64_t> policy_cells;
   std::vector<int32_t> order;             // problems by rank: longest horizon (infinite) first
+  std::vector<uint8_t> fixed_h;           // total states: 1 reach, 2 avoid (planned out of the tiles)
   int32_t* rank_of = nullptr;             // device copies for the running-prefix bound
   int32_t* rank_tile_end = nullptr;
   std::vector<double> v_offset, v_scale;  // V = offset + scale * W (reward: affine map; reach: 0, 1)
@@ -280,6 +284,9 @@ struct Session {
   // Upload a tile plan (tiles and wide states of every problem) and point the
   // launch at it.
   imdp_status install_plan(const std::vector<Tile>& tiles, const std::vector<int2>& wide, cudaStream_t st);
+  // Tile plan of every problem (rank order) under the plan limits of `c`,
+  // leaving out the states the properties fix.
+  void build_plan(const LaunchConfig& c, std::vector<Tile>& tiles, std::vector<int2>& wide) const;
   // Use launch configuration `c` from the next step on (re-plans the tiles
   // when its plan limits differ; drops the captured graph).
   imdp_status set_launch(const LaunchConfig& c, cudaStream_t st);

@@ -427,6 +427,9 @@ imdp_status model_create_csc(int32_t n_states, int32_t n_cols, int64_t nnz, cons
     if (m->n_exact == 0) {  // no correction column: nothing reads the offsets
       cudaFreeAsync(m->xoff, st);
       m->xoff = nullptr;
+    } else {
+      xo.resize(n_cols);
+      m->h_xoff = std::move(xo);  // the tile planner stages each tile's correction entries
     }
     m->bytes = m->bytes - sizeof(ulonglong2) * nz + sizeof(uint2) * nz32 + sizeof(int32_t) * nc_pad +
                (m->xoff ? sizeof(int32_t) * nc_pad : 0) + sizeof(ulonglong2) * (size_t)xn;

@@ -27,9 +27,11 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// V_0 = 1_G in both value buffers (states the property fixes are in no tile,
+// so no launch writes them).
 __global__ void srv_init_kernel(int32_t n, const uint8_t* __restrict__ fixed, uint64_t* __restrict__ V0) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    V0[i] = fixed[i] == 1 ? kOne : 0ull;
+    V0[i] = V0[n + i] = fixed[i] == 1 ? kOne : 0ull;
 }
 
 __global__ void srv_export_kernel(int32_t n, const uint64_t* __restrict__ W, double offset, double scale_v,
@@ -93,6 +95,8 @@ struct Request {
   int32_t k = 0;
   imdp_status status = IMDP_EPENDING;
   bool done = false;
+  std::vector<Tile> tiles;     // tile plan under the server's launch configuration (fixed states left out)
+  std::vector<int32_t> wide;   // wide states
 };
 
 size_t working_bytes(const DevModel* m, const imdp_spec* sp) {
@@ -136,6 +140,7 @@ struct Server {
   size_t tile_cap = 0;
   std::vector<Problem> probs_h;
   imdp_status fatal = IMDP_OK;
+  LaunchConfig cfg;  // kernel shape and tile plan limits of the launches (worker reads it under mu)
 
   explicit Server(size_t budget) : arena(budget) {}
   ~Server() {
@@ -205,6 +210,12 @@ struct Server {
       for (int32_t v : r->reach) f[v] = 1;
       for (int32_t v : r->avoid) f[v] = 2;
     }
+    {
+      const LaunchConfig rc = resolve_launch(StepLaunch{}, &cfg);
+      r->tiles.clear();
+      r->wide.clear();
+      plan_tiles(m, 0, r->tiles, r->wide, rc.tile_entries, rc.wide_col, f.data());
+    }
     cudaError_t e = cudaMemsetAsync(mask, 0, padded_u8(n), stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(mask, f.data(), n, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(hints, 0xff, padded_i32(m->n_cols) * sizeof(int32_t), stream);
@@ -262,10 +273,12 @@ struct Server {
       Request* r = slots[s];
       if (!r) continue;
       const size_t at = tiles.size();
-      tiles.insert(tiles.end(), r->model->h_tiles.begin(), r->model->h_tiles.end());
-      for (size_t t = at; t < tiles.size(); ++t) tiles[t].p = s;
-      for (int32_t st : r->model->h_wide) wide.push_back(make_int2(s, st));
-      cols += r->model->tile_cols;
+      tiles.insert(tiles.end(), r->tiles.begin(), r->tiles.end());
+      for (size_t t = at; t < tiles.size(); ++t) {
+        tiles[t].p = s;
+        cols += tiles[t].c1 - tiles[t].c0;
+      }
+      for (int32_t st : r->wide) wide.push_back(make_int2(s, st));
     }
     if (wide.size() > wide_cap) {
       cudaFree(d_wide);
@@ -401,8 +414,13 @@ struct Server {
       L.n_wide = n_wide;
       const int grid = bellman_grid();
       TraceRange trace("imdp server chunk");
+      LaunchConfig lc;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        lc = cfg;
+      }
       cudaError_t e = cudaSuccess;
-      for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = launch_bellman_step(L, grid, stream, &side);
+      for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = launch_bellman_step(L, grid, stream, &side, &lc);
       its.resize(count);
       StepControl c{};
       if (e == cudaSuccess) e = cudaMemcpyAsync(its.data(), d_its, sizeof(IterState) * count, cudaMemcpyDeviceToHost, stream);
@@ -444,6 +462,24 @@ struct imdp_server {
 };
 
 extern "C" {
+
+imdp_status imdp_server_set_launch(imdp_server* srv, const imdp_launch_config* cfg) {
+  set_error("");
+  if (!srv || !srv->s || !cfg) { set_error("NULL server or configuration"); return IMDP_EINVAL; }
+  if (cfg->kernel < 0 || cfg->kernel > 2 || cfg->tile_entries < 0 || cfg->wide_col < 0) {
+    set_error("bad launch configuration");
+    return IMDP_EINVAL;
+  }
+  LaunchConfig c;
+  c.kernel = cfg->kernel;
+  c.cta_warps = cfg->cta_warps;
+  c.ctas_per_sm = cfg->ctas_per_sm;
+  c.tile_entries = cfg->tile_entries;
+  c.wide_col = cfg->wide_col;
+  std::lock_guard<std::mutex> lk(srv->s->mu);
+  srv->s->cfg = c;  // requests admitted from now on are planned with its limits
+  return IMDP_OK;
+}
 
 imdp_status imdp_server_create(size_t hbm_budget, imdp_server** out) {
   set_error("");

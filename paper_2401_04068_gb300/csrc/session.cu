@@ -164,14 +164,10 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
     const int64_t kb = specs[b]->infinite_time ? INT64_MAX : specs[b]->horizon;
     return ka > kb;
   });
+  S->fixed_h = fixed;
   std::vector<Tile> tiles;
   std::vector<int2> wide;
-  for (int p : S->order) {
-    const size_t at = tiles.size();
-    tiles.insert(tiles.end(), ms[p]->h_tiles.begin(), ms[p]->h_tiles.end());
-    for (size_t t = at; t < tiles.size(); ++t) tiles[t].p = p;
-    for (int32_t s : ms[p]->h_wide) wide.push_back(make_int2(p, s));
-  }
+  S->build_plan(S->cfg, tiles, wide);
   S->rank_of = S->alloc<int32_t>(count);
   S->rank_tile_end = S->alloc<int32_t>(count);
   // each problem's hint block starts on a 16-byte boundary and is padded, so
@@ -333,18 +329,23 @@ imdp_status Session::install_plan(const std::vector<Tile>& tl, const std::vector
   return IMDP_OK;
 }
 
+void Session::build_plan(const LaunchConfig& c, std::vector<Tile>& tl, std::vector<int2>& wl) const {
+  const LaunchConfig r = resolve_launch(L, &c);
+  for (int p : order) {
+    std::vector<int32_t> ws;
+    const size_t at = tl.size();
+    plan_tiles(models[p], p, tl, ws, r.tile_entries, r.wide_col, fixed_h.data() + base_h[p]);
+    for (size_t t = at; t < tl.size(); ++t) tl[t].p = p;
+    for (int32_t s : ws) wl.push_back(make_int2(p, s));
+  }
+}
+
 imdp_status Session::set_launch(const LaunchConfig& c, cudaStream_t st) {
   const LaunchConfig old = resolve_launch(L, &cfg), now = resolve_launch(L, &c);
   if (now.tile_entries != old.tile_entries || now.wide_col != old.wide_col) {
     std::vector<Tile> tl;
     std::vector<int2> wl;
-    for (int p : order) {
-      std::vector<int32_t> ws;
-      const size_t at = tl.size();
-      plan_tiles(models[p], p, tl, ws, now.tile_entries, now.wide_col);
-      for (size_t t = at; t < tl.size(); ++t) tl[t].p = p;
-      for (int32_t s : ws) wl.push_back(make_int2(p, s));
-    }
+    build_plan(c, tl, wl);
     imdp_status r = install_plan(tl, wl, st);
     if (r != IMDP_OK) return r;
   }
@@ -365,8 +366,13 @@ imdp_status Session::reset(cudaStream_t st) {
     cudaGraphExecDestroy(graph);
     graph = nullptr;
   }
+  // both buffers: states the property fixes are in no tile, so no launch writes them
   init_values_kernel<<<(int)std::min<int64_t>((total + 255) / 256, 8192), 256, 0, st>>>(total, fixed, V);
   cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    init_values_kernel<<<(int)std::min<int64_t>((total + 255) / 256, 8192), 256, 0, st>>>(total, fixed, V + total);
+    e = cudaGetLastError();
+  }
   for (int p = 0; p < count && e == cudaSuccess; ++p)
     if (w0[p]) e = cudaMemcpyAsync(probs_h[p].V[0], w0[p], sizeof(uint64_t) * probs_h[p].n_states,
                                    cudaMemcpyDeviceToDevice, st);

@@ -61,3 +61,14 @@ def test_reference_arm_prints_the_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_algorithmic_bytes_leave_out_fixed_states():
+    # the reach targets' columns are read by no launch: their transitions,
+    # columns and states leave the byte count
+    m = banded_imdp(50, 2, 50 * 2 * 6 + 50 * 2 + 1, seed=3)
+    full = bench.algorithmic_bytes_per_iteration(m)
+    g = np.asarray(m.goal)
+    ent = sum(int(m.colptr[m.stateptr[s + 1]] - m.colptr[m.stateptr[s]]) for s in g)
+    cols = sum(int(m.stateptr[s + 1] - m.stateptr[s]) for s in g)
+    assert bench.algorithmic_bytes_per_iteration(m, fixed=g) == full - 20 * ent - 12 * cols - 20 * len(g)

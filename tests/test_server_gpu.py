@@ -21,7 +21,9 @@ def _wait(server, ticket, n):
     return st, V, k[0], lat[0]
 
 
-def test_server_mixed_stream_matches_alone():
+@pytest.mark.parametrize("launch", [None, dict(kernel=g.KERNEL_DIRECT, ctas_per_sm=4, tile_entries=1024),
+                                    dict(kernel=g.KERNEL_RING, cta_warps=16, wide_col=300)])
+def test_server_mixed_stream_matches_alone(launch):
     models_in = [banded_imdp(300, 2, 300 * 2 * 20 + 1, seed=60),
                  banded_imdp(150, 3, 150 * 3 * 12 + 1, seed=61),
                  random_imdp(40, max_actions=3, seed=62)]
@@ -43,6 +45,8 @@ def test_server_mixed_stream_matches_alone():
                                discount=0.9, pessimistic=False)
         reqs.append((j, spec))
     server = g.imdp_server_create(256 << 20)
+    if launch:  # every launch configuration computes the same words
+        g.imdp_server_set_launch(server, **launch)
     tickets = []
     for i, (j, spec) in enumerate(reqs):
         tickets.append(g.imdp_server_submit(server, models[j], spec))
