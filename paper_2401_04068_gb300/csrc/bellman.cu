@@ -381,116 +381,6 @@ __device__ __forceinline__ uint64_t mul_shr(uint64_t a, uint64_t b, int s) {
 // x << d, saturating at 2^64 - 1.
 __device__ __forceinline__ uint64_t shl_sat(uint64_t x, int d) { return (x >> (64 - d)) ? ~0ull : x << d; }
 
-// Per-warp streaming ring of the direct kernel's warm pass: every lane copies
-// its own entries (destination and bound pair) of trips t + 1 .. t + kRingDepth
-// into shared memory with cp.async while trip t is computed, so that a warp
-// keeps kRingDepth trips of loads in flight without holding them in
-// registers. Entries past the column's end are zero-filled by the copy (source
-// size 0: nothing is read), which is what the warm pass's padding lanes use.
-constexpr int kRingDepth = 4;
-constexpr int kRingSlots = kRingDepth + 1;  // the slot being refilled is never the one being read
-struct StreamRing {
-  int32_t rows[kRingSlots][32];
-  ulonglong2 lg[kRingSlots][32];  // 32-bit storage uses the first half of each slot as uint2[32]
-};
-
-__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool ok) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(ok ? 4 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool ok) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(ok ? 8 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool ok) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(ok ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Copies of trip t (this lane's entry) into its ring slot, then one commit
-// (an empty group past the last trip, so that every trip is one group).
-template <bool f32>
-__device__ __forceinline__ void ring_issue(StreamRing* R, int slot, const int32_t* rows, const void* lg, int t,
-                                           int nb, int32_t k, int lane) {
-  if (t < nb) {
-    const int idx = t * 32 + lane;
-    const bool ok = idx < k;
-    const int i = ok ? idx : 0;
-    cp_async4(&R->rows[slot][lane], rows + i, ok);
-    if (f32)
-      cp_async8(reinterpret_cast<uint2*>(&R->lg[slot][0]) + lane, static_cast<const uint2*>(lg) + i, ok);
-    else
-      cp_async16(&R->lg[slot][lane], static_cast<const ulonglong2*>(lg) + i, ok);
-  }
-  cp_async_commit();
-}
-
-// warm_pass (64-bit storage) over a column in global memory, fed by the ring.
-template <bool carry>
-__device__ __forceinline__ void warm_pass_ring(const int32_t* rows, const ulonglong2* lg, int32_t k,
-                                               const uint64_t* __restrict__ V, uint64_t vk, bool pess, int lane,
-                                               uint64_t& acc, uint64_t& flt, uint64_t& geq, StreamRing* R) {
-  uint32_t fc = 0, gc = 0;
-  const int nb = (k + 31) >> 5;
-#pragma unroll
-  for (int t = 0; t < kRingDepth; ++t) ring_issue<false>(R, t, rows, lg, t, nb, k, lane);
-  int slot = 0, fill = kRingDepth;
-  for (int it = 0; it < nb; ++it) {
-    cp_async_wait<kRingDepth - 1>();  // trip `it` has landed
-    const int32_t r = R->rows[slot][lane];
-    const ulonglong2 b = R->lg[slot][lane];
-    ring_issue<false>(R, fill, rows, lg, it + kRingDepth, nb, k, lane);
-    slot = slot + 1 == kRingSlots ? 0 : slot + 1;
-    fill = fill + 1 == kRingSlots ? 0 : fill + 1;
-    const uint64_t v = ld_value(V + r);
-    const bool below = pess ? (v < vk) : (v > vk);
-    acc += __umul64hi(v, b.x + (below ? b.y : 0ull));
-    const uint64_t gb = below ? b.y : 0ull, ge = v == vk ? b.y : 0ull;
-    flt += gb;
-    geq += ge;
-    if (carry) {
-      fc += flt < gb ? 1u : 0u;
-      gc += geq < ge ? 1u : 0u;
-    }
-  }
-  cp_async_wait<0>();
-  if (carry) {
-    flt = fc ? ~0ull : flt;
-    geq = gc ? ~0ull : geq;
-  }
-}
-
-// warm_pass32 over a column in global memory, fed by the ring.
-__device__ __forceinline__ void warm_pass32_ring(const int32_t* rows, const uint2* m, int32_t k,
-                                                 const uint64_t* __restrict__ V, uint32_t vk, int s, bool pess,
-                                                 int lane, uint64_t& acc, uint64_t& flt, uint64_t& geq,
-                                                 StreamRing* R) {
-  const int nb = (k + 31) >> 5;
-#pragma unroll
-  for (int t = 0; t < kRingDepth; ++t) ring_issue<true>(R, t, rows, m, t, nb, k, lane);
-  int slot = 0, fill = kRingDepth;
-  for (int it = 0; it < nb; ++it) {
-    cp_async_wait<kRingDepth - 1>();
-    const int32_t r = R->rows[slot][lane];
-    const uint2 b = reinterpret_cast<const uint2*>(&R->lg[slot][0])[lane];
-    ring_issue<true>(R, fill, rows, m, it + kRingDepth, nb, k, lane);
-    slot = slot + 1 == kRingSlots ? 0 : slot + 1;
-    fill = fill + 1 == kRingSlots ? 0 : fill + 1;
-    const uint32_t v = ld_value_hi(V + r);
-    const bool below = pess ? (v < vk) : (v > vk);
-    const uint32_t g = below ? b.y : 0u;
-    acc += ((uint64_t)v * (uint64_t)(b.x + g)) >> s;
-    flt += g;
-    geq += v == vk ? b.y : 0u;
-  }
-  cp_async_wait<0>();
-}
-
 // `rem_word` is rem = 1 - sum(lower) in Q1.63 (<= 2^63); when 0 < rem < 2^63 and
 // the column's gaps add up to < 2^64 ("narrow"), model creation sets bit 63 as a
 // flag on top of rem.
@@ -515,7 +405,7 @@ struct WarmMiss {
 template <bool f32, bool gmem>
 __device__ __forceinline__ bool column_warm(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem_word,
                                             const uint64_t* __restrict__ V, bool pess, int lane, int32_t hint,
-                                            uint64_t* q, WarmMiss* miss, StreamRing* ring = nullptr) {
+                                            uint64_t* q, WarmMiss* miss) {
   miss->valid = false;
   const uint64_t rem = rem_of(rem_word);
   if (rem == 0) {
@@ -531,14 +421,7 @@ __device__ __forceinline__ bool column_warm(const typename RowsOf<gmem>::type ro
     const int down = lg.down, sh = 32 - down;
     const uint32_t vk32 = ld_value_hi(V + rows[hint]);
     uint64_t acc = 0, flt = 0, geq = 0;
-    if constexpr (gmem) {
-      if (ring)
-        warm_pass32_ring(rows.p, static_cast<const uint2*>(lg.p), k, V, vk32, sh, pess, lane, acc, flt, geq, ring);
-      else
-        warm_pass32<gmem>(rows, static_cast<const uint2*>(lg.p), k, V, vk32, sh, pess, lane, acc, flt, geq);
-    } else {
-      warm_pass32<gmem>(rows, static_cast<const uint2*>(lg.p), k, V, vk32, sh, pess, lane, acc, flt, geq);
-    }
+    warm_pass32<gmem>(rows, static_cast<const uint2*>(lg.p), k, V, vk32, sh, pess, lane, acc, flt, geq);
     acc = warp_sum_u64(acc);
     flt = warp_sum_u64(flt);
     geq = warp_sum_u64(geq);
@@ -552,25 +435,7 @@ __device__ __forceinline__ bool column_warm(const typename RowsOf<gmem>::type ro
   }
   const uint64_t vk = ld_value(V + rows[hint]);
   uint64_t acc = 0, flt = 0, geq = 0;
-  bool streamed = false;
-  if constexpr (gmem && !f32) {
-    if (ring) {  // the direct kernel: loads in flight through the ring
-      if (narrow_of(rem_word))
-        warm_pass_ring<false>(rows.p, static_cast<const ulonglong2*>(lg.p), k, V, vk, pess, lane, acc, flt, geq, ring);
-      else
-        warm_pass_ring<true>(rows.p, static_cast<const ulonglong2*>(lg.p), k, V, vk, pess, lane, acc, flt, geq, ring);
-      streamed = true;
-    }
-  }
-  if (streamed) {
-    if (narrow_of(rem_word)) {
-      flt = warp_sum_u64(flt);
-      geq = warp_sum_u64(geq);
-    } else {
-      flt = warp_sum_sat(flt);
-      geq = warp_sum_sat(geq);
-    }
-  } else if (narrow_of(rem_word)) {
+  if (narrow_of(rem_word)) {
     // every gap sum of a narrow column is below 2^64: plain exact sums
     warm_pass<false, f32, gmem>(rows, lg, k, V, vk, pess, lane, acc, flt, geq);
     flt = warp_sum_u64(flt);
@@ -833,7 +698,7 @@ __device__ uint64_t column_search(const typename RowsOf<gmem>::type rows, const 
 template <bool f32, bool gmem>
 __device__ uint64_t column_q(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem_word,
                              const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane, int32_t hint,
-                             int32_t* hint_out, StreamRing* ring = nullptr) {
+                             int32_t* hint_out) {
   // A hint of -2 - i names entry i as well and records that the column's last
   // value came from the full search: its threshold is moving fast, so a miss
   // goes to the search without trying the neighbour.
@@ -841,7 +706,7 @@ __device__ uint64_t column_q(const typename RowsOf<gmem>::type rows, const Bound
   const int32_t entry = moving ? -2 - hint : hint;
   uint64_t q;
   WarmMiss miss;
-  if (column_warm<f32, gmem>(rows, lg, k, rem_word, V, pess, lane, entry, &q, &miss, ring)) {
+  if (column_warm<f32, gmem>(rows, lg, k, rem_word, V, pess, lane, entry, &q, &miss)) {
     *hint_out = entry;
     return q;
   }
@@ -1248,8 +1113,7 @@ struct ColChunk {
 };
 
 template <bool f32>
-__device__ void direct_tile(const StepLaunch& L, const Tile& T, int32_t k_iter, WarpScratch* ws, StreamRing* ring,
-                            int lane) {
+__device__ void direct_tile(const StepLaunch& L, const Tile& T, int32_t k_iter, WarpScratch* ws, int lane) {
   const Problem& P = L.probs[T.p];
   const uint64_t* __restrict__ Vin = P.V[(k_iter - 1) & 1];
   uint64_t* __restrict__ Vout = P.V[k_iter & 1];
@@ -1316,13 +1180,13 @@ __device__ void direct_tile(const StepLaunch& L, const Tile& T, int32_t k_iter, 
           if (f32 && xo < 0)
             q = column_q<true, true>(GRows{P.rowval + ca},
                                      Bounds<true, true>{P.lg32 + ca, 32 - __shfl_sync(kFull, cc.shift, src)}, ce - ca,
-                                     rw, Vin, pess, ws, lane, h, &hout, ring);
+                                     rw, Vin, pess, ws, lane, h, &hout);
           else if (f32)  // correction column: its exact bounds
             q = column_q<false, true>(GRows{P.rowval + ca}, Bounds<false, true>{P.lgx + xo, 0}, ce - ca, rw, Vin,
-                                      pess, ws, lane, h, &hout, ring);
+                                      pess, ws, lane, h, &hout);
           else
             q = column_q<false, true>(GRows{P.rowval + ca}, Bounds<false, true>{P.lg + ca, 0}, ce - ca, rw, Vin, pess,
-                                      ws, lane, h, &hout, ring);
+                                      ws, lane, h, &hout);
           if (lane == 0 && hint && hout != h) hint[c] = hout;
           if (best < 0 || (maxi ? q > bq : q < bq)) {
             bq = q;
@@ -1340,7 +1204,6 @@ __device__ void direct_tile(const StepLaunch& L, const Tile& T, int32_t k_iter, 
 template <int NW, int MINB>
 __global__ void __launch_bounds__(32 * NW, MINB) bellman_direct_kernel(StepLaunch L) {
   __shared__ WarpScratch ws_all[NW];
-  __shared__ StreamRing rings[NW];
   __shared__ int is_last;
   const int lane = threadIdx.x & 31;
   WarpScratch* ws = &ws_all[threadIdx.x >> 5];
@@ -1354,9 +1217,9 @@ __global__ void __launch_bounds__(32 * NW, MINB) bellman_direct_kernel(StepLaunc
     int32_t k_iter;
     if (!problem_active(L, T.p, &k_iter)) continue;
     if (L.probs[T.p].lg32)
-      direct_tile<true>(L, T, k_iter, ws, &rings[threadIdx.x >> 5], lane);
+      direct_tile<true>(L, T, k_iter, ws, lane);
     else
-      direct_tile<false>(L, T, k_iter, ws, &rings[threadIdx.x >> 5], lane);
+      direct_tile<false>(L, T, k_iter, ws, lane);
   }
   end_of_launch(L, &is_last);
 }
