@@ -739,6 +739,7 @@ def run_served(args, rank, world, local_rank):
     ok = all(d[0] == g.IMDP_OK and d[1] == r[1] for d, r in zip(done, reqs))
     span = max(d[2] for d in done) - t0
     units = float(sum(models_h[r[0]].nnz * r[1] for r in reqs))
+    stats = g.imdp_server_stats(server)
     server.close()
     if rank != 0:
         return
@@ -755,6 +756,11 @@ def run_served(args, rank, world, local_rank):
                    "all_ok": bool(ok)},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
                        "p99": float(np.percentile(lat, 99)), "mean": float(lat.mean()), "max": float(lat.max())},
+        # the stream's own rate: work of all requests over the span of their arrivals
+        "offered_updates_per_s": units / float(arrivals[-1]),
+        # the worker's time: device time of the launches against its wall time (the rest is
+        # read-back, retirement, admission and table uploads between chunks)
+        "server": dict(stats, device_busy=stats["device_ms"] / max(1e-9, stats["wall_ms"])),
         "client": {"model_create_ms_mean": 1e3 * float(np.mean(create_s)) if create_s else 0.0,
                    "model_create_s_total": float(np.sum(create_s)),
                    "submits_behind_schedule": len(lag_s),

@@ -427,6 +427,14 @@ IMDP_API imdp_status imdp_server_create(size_t hbm_budget, imdp_server** out);
  * limits; it may change while requests run (a running request keeps its plan).
  * Thread-safe. IMDP_EINVAL for NULL or a bad configuration. */
 IMDP_API imdp_status imdp_server_set_launch(imdp_server* s, const imdp_launch_config* cfg);
+/* Where the server's time went since its creation (no counterpart in the paper):
+ * device_ms = the device time of its Bellman launches (CUDA events around each
+ * chunk), wall_ms = the worker's time while requests were admitted or running
+ * (launches, read-back, retirement, admission, table uploads), chunks = chunks of
+ * launches, mean_requests = requests in a chunk's launches on average. Any
+ * output may be NULL. Thread-safe. */
+IMDP_API imdp_status imdp_server_stats(imdp_server* s, double* device_ms, double* wall_ms, int64_t* chunks,
+                                       double* mean_requests);
 /* Queue a request; returns at once with a ticket. IMDP_ENOMEM if the request
  * alone exceeds the budget, IMDP_EBUSY if the queue is full. */
 IMDP_API imdp_status imdp_server_submit(imdp_server* s, imdp_model* m, const imdp_spec* spec, uint64_t* ticket);

@@ -35,7 +35,7 @@ EXPORTED = [
     "imdp_session_checkpoint", "imdp_session_restore",
     "imdp_session_set_launch", "imdp_session_get_launch", "imdp_session_autotune", "imdp_session_plan",
     "imdp_create_csc_f32", "imdp_model_exact_columns", "imdp_session_residual", "imdp_session_stop_threshold",
-    "imdp_server_set_launch",
+    "imdp_server_set_launch", "imdp_server_stats",
 ]
 
 
@@ -133,6 +133,8 @@ def load(path: Optional[str] = None):
     lib.imdp_session_get_launch.argtypes = [vp, C.POINTER(imdp_launch_config)]
     lib.imdp_session_plan.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
     lib.imdp_server_set_launch.argtypes = [vp, C.POINTER(imdp_launch_config)]
+    lib.imdp_server_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_double)]
     lib.imdp_session_residual.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, vp]
     lib.imdp_session_stop_threshold.argtypes = [vp, C.c_int32, C.POINTER(C.c_uint64)]
     lib.imdp_session_autotune.argtypes = [vp, C.c_int32, C.c_char_p, vp, C.POINTER(imdp_launch_config),
@@ -506,6 +508,14 @@ def imdp_server_set_launch(server: Server, kernel: int = 0, cta_warps: int = 0, 
     """Launch configuration of the server's Bellman launches (0 fields: by rule)."""
     cfg = imdp_launch_config(kernel, cta_warps, ctas_per_sm, tile_entries, wide_col)
     _check(load().imdp_server_set_launch(C.c_void_p(server.handle), C.byref(cfg)), "imdp_server_set_launch")
+
+
+def imdp_server_stats(server: Server) -> dict:
+    """Device time, worker wall time, chunks and mean requests per chunk of a server."""
+    d, w, c, r = C.c_double(0), C.c_double(0), C.c_int64(0), C.c_double(0)
+    _check(load().imdp_server_stats(C.c_void_p(server.handle), C.byref(d), C.byref(w), C.byref(c), C.byref(r)),
+           "imdp_server_stats")
+    return dict(device_ms=d.value, wall_ms=w.value, chunks=c.value, mean_requests=r.value)
 
 
 def imdp_server_submit(server: Server, model: Model, spec) -> int:

@@ -141,6 +141,12 @@ struct Server {
   std::vector<Problem> probs_h;
   imdp_status fatal = IMDP_OK;
   LaunchConfig cfg;  // kernel shape and tile plan limits of the launches (worker reads it under mu)
+  // statistics (worker thread; read under mu): device time of the chunks (CUDA
+  // events around each chunk's launches), wall time of the loop while requests
+  // were running, chunks, and requests in the launches summed over chunks
+  double st_device_ms = 0.0, st_wall_ms = 0.0, st_slots = 0.0;
+  int64_t st_chunks = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
   explicit Server(size_t budget) : arena(budget) {}
   ~Server() {
@@ -159,6 +165,8 @@ struct Server {
     cudaFree(d_base);
     cudaFree(d_tiles);
     cudaFree(d_wide);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
     side.destroy();
     for (auto& kv : all) delete kv.second;
   }
@@ -356,6 +364,7 @@ struct Server {
     int32_t count = 0;  // slots [0, count) are in the launch
     while (true) {
       bool changed = false;
+      const Clock::time_point h0 = Clock::now();
       {
         std::unique_lock<std::mutex> lk(mu);
         bool any_active = false;
@@ -399,6 +408,7 @@ struct Server {
           return;
         }
       }
+      pending_host_ms = std::chrono::duration<double, std::milli>(Clock::now() - h0).count();
       StepLaunch L{};
       L.probs = d_probs;
       L.its = d_its;
@@ -419,8 +429,15 @@ struct Server {
         std::lock_guard<std::mutex> lk(mu);
         lc = cfg;
       }
+      const Clock::time_point w0 = Clock::now();
       cudaError_t e = cudaSuccess;
+      if (!ev0) {
+        e = cudaEventCreate(&ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(ev0, stream);
       for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = launch_bellman_step(L, grid, stream, &side, &lc);
+      if (e == cudaSuccess) e = cudaEventRecord(ev1, stream);
       its.resize(count);
       StepControl c{};
       if (e == cudaSuccess) e = cudaMemcpyAsync(its.data(), d_its, sizeof(IterState) * count, cudaMemcpyDeviceToHost, stream);
@@ -437,12 +454,27 @@ struct Server {
         cv.notify_all();
         return;
       }
+      float dev_ms = 0.f;
+      cudaEventElapsedTime(&dev_ms, ev0, ev1);
+      int active = 0;
       for (int s = 0; s < count; ++s) {
         Request* r = slots[s];
+        active += r ? 1 : 0;
         if (r && its[s].done) retire(r, its[s]);
       }
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        st_device_ms += dev_ms;
+        st_chunks += 1;
+        st_slots += active;
+        // wall time from this chunk's launches to the end of its retirements;
+        // admission and table uploads before the next chunk are added there
+        st_wall_ms += std::chrono::duration<double, std::milli>(Clock::now() - w0).count() + pending_host_ms;
+      }
+      pending_host_ms = 0.0;
     }
   }
+  double pending_host_ms = 0.0;  // admission and table work before the next chunk (worker only)
 
   static uint64_t eps_fixed(double eps) {
     if (eps >= 1.0) return kOne + 1;
@@ -462,6 +494,19 @@ struct imdp_server {
 };
 
 extern "C" {
+
+imdp_status imdp_server_stats(imdp_server* srv, double* device_ms, double* wall_ms, int64_t* chunks,
+                              double* mean_requests) {
+  set_error("");
+  if (!srv || !srv->s) { set_error("NULL server"); return IMDP_EINVAL; }
+  Server* S = srv->s;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (device_ms) *device_ms = S->st_device_ms;
+  if (wall_ms) *wall_ms = S->st_wall_ms;
+  if (chunks) *chunks = S->st_chunks;
+  if (mean_requests) *mean_requests = S->st_chunks ? S->st_slots / (double)S->st_chunks : 0.0;
+  return IMDP_OK;
+}
 
 imdp_status imdp_server_set_launch(imdp_server* srv, const imdp_launch_config* cfg) {
   set_error("");

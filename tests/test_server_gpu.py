@@ -62,6 +62,9 @@ def test_server_mixed_stream_matches_alone(launch):
         g.imdp_value_iteration(models[j], spec, alone, ka)
         assert k == ka[0]
         np.testing.assert_array_equal(V, alone)
+    st = g.imdp_server_stats(server)
+    assert st["chunks"] > 0 and st["mean_requests"] >= 1.0
+    assert 0.0 < st["device_ms"] <= 1.05 * st["wall_ms"] + 1.0  # the worker waits for its launches
     server.close()
 
 
