@@ -276,7 +276,8 @@ IMDP_API imdp_status imdp_session_run(imdp_session* s, int32_t check_every, void
 IMDP_API imdp_status imdp_session_read(imdp_session* s, int32_t index, double* V_out, int32_t* k_out,
                                        double* residual_out, int32_t* policy_out, void* stream);
 
-/* Number of step-kernel launches issued by the session so far. */
+/* Bellman iterations launched by the session so far (one kernel launch each,
+ * except on the single-CTA kernel, which runs a step call's iterations in one). */
 IMDP_API int64_t imdp_session_launches(const imdp_session* s);
 
 IMDP_API void imdp_session_destroy(imdp_session* s);
@@ -285,10 +286,15 @@ IMDP_API void imdp_session_destroy(imdp_session* s);
  * Launch configuration of a session's Bellman step (no counterpart in the
  * paper, whose GPU kernels have one fixed shape). Every configuration computes
  * the same words; they differ in speed only. Zero fields mean "by rule".
- *   kernel        0 by rule (ring); 1 ring: a producer warp bulk-copies tiles of
+ *   kernel        0 by rule (the single-CTA kernel for a session of one small
+ *                 problem, else ring); 1 ring: a producer warp bulk-copies tiles of
  *                 consecutive states into a three-stage shared-memory ring for
  *                 consumer warps; 2 direct: every warp takes the next tile and
- *                 streams its columns from global memory itself
+ *                 streams its columns from global memory itself; 3 single CTA:
+ *                 one CTA keeps the model and its values in shared memory and
+ *                 runs every iteration of a step call in one launch (sessions of
+ *                 one problem with at most 1024 states, 1024 columns and 4096
+ *                 transitions that is not a slice; IMDP_EINVAL otherwise)
  *   cta_warps     ring: 16 or 24 warps per CTA (24 only without wide states; rule:
  *                 24 when the tiles hold 16 or more columns on average); direct: 8
  *   ctas_per_sm   direct: 3 or 4 (rule 4); ring: 1

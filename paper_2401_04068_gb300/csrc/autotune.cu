@@ -177,8 +177,12 @@ extern "C" {
 IMDP_API imdp_status imdp_session_set_launch(imdp_session* s, const imdp_launch_config* cfg, void* stream) {
   set_error("");
   if (!s || !s->s || !cfg) { set_error("NULL session or configuration"); return IMDP_EINVAL; }
-  if (cfg->kernel < 0 || cfg->kernel > 2 || cfg->tile_entries < 0 || cfg->wide_col < 0) {
+  if (cfg->kernel < 0 || cfg->kernel > 3 || cfg->tile_entries < 0 || cfg->wide_col < 0) {
     set_error("bad launch configuration");
+    return IMDP_EINVAL;
+  }
+  if (cfg->kernel == kKernelTiny && !s->s->L.tiny_ok) {
+    set_error("the single-CTA kernel runs one problem of at most 1024 states, 1024 columns and 4096 transitions");
     return IMDP_EINVAL;
   }
   DeviceScope g(s->s->device);
@@ -243,6 +247,7 @@ IMDP_API imdp_status imdp_session_autotune(imdp_session* s, int32_t iters, const
       c.wide_col = wc;
       cands.push_back(c);
     };
+    if (S->L.tiny_ok) add(kKernelTiny, 0, 0, kTileEntries, kWideCol);
     add(kKernelRing, 16, 1, kTileEntries, kWideCol);
     if (!wide_default) add(kKernelRing, 24, 1, kTileEntries, kWideCol);
     add(kKernelDirect, kDirectWarps, 4, kTileEntries, kWideCol);
@@ -259,7 +264,7 @@ IMDP_API imdp_status imdp_session_autotune(imdp_session* s, int32_t iters, const
       }
     }
     // stage 2: the wide-state threshold, for models with long columns
-    if (r == IMDP_OK && max_col >= 640) {
+    if (r == IMDP_OK && max_col >= 640 && best.kernel != kKernelTiny) {
       for (int32_t wc : {640, 2560, 1 << 30}) {
         LaunchConfig c = best;
         c.wide_col = wc;

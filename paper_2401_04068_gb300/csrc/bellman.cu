@@ -311,15 +311,31 @@ struct Bounds {
   }
 };
 
+// Where the column routines read V_{k-1}: gathers from global memory (the
+// tiled kernels; read-only during a launch, L1 evict-last), or from shared
+// memory (the single-CTA kernel, which keeps a small problem's values there
+// across its iterations). `hi` is the high word, the whole value of a problem
+// on 32-bit storage.
+struct GlobalV {
+  const uint64_t* p;
+  __device__ __forceinline__ uint64_t at(int32_t r) const { return ld_value(p + r); }
+  __device__ __forceinline__ uint32_t hi(int32_t r) const { return ld_value_hi(p + r); }
+};
+struct SharedV {
+  const uint64_t* p;
+  __device__ __forceinline__ uint64_t at(int32_t r) const { return p[r]; }
+  __device__ __forceinline__ uint32_t hi(int32_t r) const { return (uint32_t)(p[r] >> 32); }
+};
+
 // One pass of the warm start over a column: acc = sum of V times (upper below
 // v_k, lower elsewhere), flt = gap sum of the entries below v_k, geq = gap sum of
 // the entries at v_k. The trip count is warp-uniform; padding entries read row 0
 // and contribute zero. With `carry` the per-lane gap sums count their wraps and
 // saturate; without it the column is narrow (all its gaps add up to < 2^64), so
 // no sum can wrap.
-template <bool carry, bool f32, bool gmem>
+template <bool carry, bool f32, bool gmem, class VP>
 __device__ __forceinline__ void warm_pass(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k,
-                                          const uint64_t* __restrict__ V, uint64_t vk, bool pess, int lane,
+                                          const VP V, uint64_t vk, bool pess, int lane,
                                           uint64_t& acc, uint64_t& flt, uint64_t& geq) {
   uint32_t fc = 0, gc = 0;
   const int nb = (k + 31) >> 5;
@@ -327,7 +343,7 @@ __device__ __forceinline__ void warm_pass(const typename RowsOf<gmem>::type rows
   for (int it = 0; it < nb; ++it) {
     const int idx = it * 32 + lane;
     const bool ok = idx < k;
-    const uint64_t v = ld_value(V + (ok ? rows[idx] : 0));
+    const uint64_t v = V.at(ok ? rows[idx] : 0);
     const ulonglong2 b = ok ? lg[idx] : make_ulonglong2(0, 0);
     const bool below = pess ? (v < vk) : (v > vk);
     acc += __umul64hi(v, b.x + (below ? b.y : 0ull));
@@ -353,16 +369,16 @@ __device__ __forceinline__ void warm_pass(const typename RowsOf<gmem>::type rows
 // and the same decisions from its gap sums (kept in mantissa units, where no
 // sum can wrap), as warm_pass on the widened bounds: one 32x32 multiply, a
 // shift and a 64-bit add per entry instead of a 64x64 multiply-high.
-template <bool gmem>
+template <bool gmem, class VP>
 __device__ __forceinline__ void warm_pass32(const typename RowsOf<gmem>::type rows, const uint2* __restrict__ m,
-                                            int32_t k, const uint64_t* __restrict__ V, uint32_t vk, int s, bool pess,
+                                            int32_t k, const VP V, uint32_t vk, int s, bool pess,
                                             int lane, uint64_t& acc, uint64_t& flt, uint64_t& geq) {
   const int nb = (k + 31) >> 5;
 #pragma unroll 2
   for (int it = 0; it < nb; ++it) {
     const int idx = it * 32 + lane;
     const bool ok = idx < k;
-    const uint32_t v = ld_value_hi(V + (ok ? rows[idx] : 0));
+    const uint32_t v = V.hi(ok ? rows[idx] : 0);
     uint2 b = make_uint2(0, 0);
     if (ok) b = gmem ? ld_stream_u32x2(m + idx) : m[idx];
     const bool below = pess ? (v < vk) : (v > vk);
@@ -402,16 +418,16 @@ struct WarmMiss {
   bool valid;
 };
 
-template <bool f32, bool gmem>
+template <bool f32, bool gmem, class VP>
 __device__ __forceinline__ bool column_warm(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem_word,
-                                            const uint64_t* __restrict__ V, bool pess, int lane, int32_t hint,
+                                            const VP V, bool pess, int lane, int32_t hint,
                                             uint64_t* q, WarmMiss* miss) {
   miss->valid = false;
   const uint64_t rem = rem_of(rem_word);
   if (rem == 0) {
     uint64_t acc = 0;
 #pragma unroll 4
-    for (int idx = lane; idx < k; idx += 32) acc += __umul64hi(ld_value(V + rows[idx]), lg[idx].x);
+    for (int idx = lane; idx < k; idx += 32) acc += __umul64hi(V.at(rows[idx]), lg[idx].x);
     *q = warp_sum_u64(acc);
     return true;
   }
@@ -419,7 +435,7 @@ __device__ __forceinline__ bool column_warm(const typename RowsOf<gmem>::type ro
   if (f32) {
     // 32-bit storage: the pass in 32-bit arithmetic (same words as below)
     const int down = lg.down, sh = 32 - down;
-    const uint32_t vk32 = ld_value_hi(V + rows[hint]);
+    const uint32_t vk32 = V.hi(rows[hint]);
     uint64_t acc = 0, flt = 0, geq = 0;
     warm_pass32<gmem>(rows, static_cast<const uint2*>(lg.p), k, V, vk32, sh, pess, lane, acc, flt, geq);
     acc = warp_sum_u64(acc);
@@ -433,7 +449,7 @@ __device__ __forceinline__ bool column_warm(const typename RowsOf<gmem>::type ro
     *miss = WarmMiss{(uint64_t)vk32 << 32, acc, shl_sat(flt, down), shl_sat(geq, down), true};
     return false;
   }
-  const uint64_t vk = ld_value(V + rows[hint]);
+  const uint64_t vk = V.at(rows[hint]);
   uint64_t acc = 0, flt = 0, geq = 0;
   if (narrow_of(rem_word)) {
     // every gap sum of a narrow column is below 2^64: plain exact sums
@@ -464,9 +480,9 @@ __device__ __forceinline__ bool column_warm(const typename RowsOf<gmem>::type ro
 //   above: F(< kappa+) = F(<= kappa), holds when F(<= kappa) + G >= rem;
 // and q is the warm formula at the new key, to the bit. Returns false when the
 // threshold moved further (or a sum is not exact), leaving the full search.
-template <bool f32, bool gmem>
+template <bool f32, bool gmem, class VP>
 __device__ __forceinline__ bool column_neighbor(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem,
-                                                const uint64_t* __restrict__ V, bool pess, int lane,
+                                                const VP V, bool pess, int lane,
                                                 const WarmMiss& w, uint64_t* q, int32_t* hint_out) {
   const bool down = w.flt >= rem;
   if (down && w.flt >= kOne) return false;  // F(< kappa) clipped: not exact
@@ -478,7 +494,7 @@ __device__ __forceinline__ bool column_neighbor(const typename RowsOf<gmem>::typ
   for (int it = 0; it < nb; ++it) {
     const int idx = it * 32 + lane;
     if (idx >= k) break;
-    const uint64_t v = ld_value(V + rows[idx]);
+    const uint64_t v = V.at(rows[idx]);
     const uint64_t key = pess ? v : kOne - v;
     const ulonglong2 b = lg[idx];
     const uint64_t d = __umul64hi(v, b.x + b.y) - __umul64hi(v, b.x);
@@ -523,13 +539,13 @@ __device__ __forceinline__ bool column_neighbor(const typename RowsOf<gmem>::typ
 
 // Threshold search over a column with rem > 0 (the warm start failed or had no
 // hint). Returns q in Q2.62 and the threshold entry in *hint_out.
-template <bool f32, bool gmem>
+template <bool f32, bool gmem, class VP>
 __device__ uint64_t column_search(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem_word,
-                                  const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane,
+                                  const VP V, bool pess, WarpScratch* ws, int lane,
                                   int32_t* hint_out) {
   const uint64_t rem = rem_of(rem_word);
   auto key_of = [&](int idx) -> uint64_t {
-    const uint64_t v = ld_value(V + rows[idx]);
+    const uint64_t v = V.at(rows[idx]);
     return pess ? v : (kOne - v);
   };
 
@@ -695,9 +711,9 @@ __device__ uint64_t column_search(const typename RowsOf<gmem>::type rows, const 
 }
 
 // One column, warm start first: q in Q2.62, the threshold entry in *hint_out.
-template <bool f32, bool gmem>
+template <bool f32, bool gmem, class VP>
 __device__ uint64_t column_q(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem_word,
-                             const uint64_t* __restrict__ V, bool pess, WarpScratch* ws, int lane, int32_t hint,
+                             const VP V, bool pess, WarpScratch* ws, int lane, int32_t hint,
                              int32_t* hint_out) {
   // A hint of -2 - i names entry i as well and records that the column's last
   // value came from the full search: its threshold is moving fast, so a miss
@@ -829,7 +845,7 @@ __device__ __forceinline__ void stage_column(Stage& st, const Tile& T, int32_t l
                                                                   (size_t)(qe - qb) * 8u);
       int32_t hout;
       const uint64_t q = column_q<false, false>(st.rows + (ca - eb), Bounds<false>{xs + (xo - T.x0), 0}, ce - ca,
-                                                st.rem[c - mb], P.V[(k_iter - 1) & 1], P.pessimistic != 0, ws, lane,
+                                                st.rem[c - mb], GlobalV{P.V[(k_iter - 1) & 1]}, P.pessimistic != 0, ws, lane,
                                                 h, &hout);
       if (lane == 0) {
         st.q[li] = q;
@@ -844,7 +860,7 @@ __device__ __forceinline__ void stage_column(Stage& st, const Tile& T, int32_t l
   else
     bd = Bounds<f32>{st.lg + (ca - T.e0), 0};
   int32_t hout;
-  const uint64_t q = column_q<f32, false>(st.rows + (ca - eb), bd, ce - ca, st.rem[c - mb], P.V[(k_iter - 1) & 1],
+  const uint64_t q = column_q<f32, false>(st.rows + (ca - eb), bd, ce - ca, st.rem[c - mb], GlobalV{P.V[(k_iter - 1) & 1]},
                                    P.pessimistic != 0, ws, lane, h, &hout);
   if (lane == 0) {
     st.q[li] = q;
@@ -1180,12 +1196,12 @@ __device__ void direct_tile(const StepLaunch& L, const Tile& T, int32_t k_iter, 
           if (f32 && xo < 0)
             q = column_q<true, true>(GRows{P.rowval + ca},
                                      Bounds<true, true>{P.lg32 + ca, 32 - __shfl_sync(kFull, cc.shift, src)}, ce - ca,
-                                     rw, Vin, pess, ws, lane, h, &hout);
+                                     rw, GlobalV{Vin}, pess, ws, lane, h, &hout);
           else if (f32)  // correction column: its exact bounds
-            q = column_q<false, true>(GRows{P.rowval + ca}, Bounds<false, true>{P.lgx + xo, 0}, ce - ca, rw, Vin,
+            q = column_q<false, true>(GRows{P.rowval + ca}, Bounds<false, true>{P.lgx + xo, 0}, ce - ca, rw, GlobalV{Vin},
                                       pess, ws, lane, h, &hout);
           else
-            q = column_q<false, true>(GRows{P.rowval + ca}, Bounds<false, true>{P.lg + ca, 0}, ce - ca, rw, Vin, pess,
+            q = column_q<false, true>(GRows{P.rowval + ca}, Bounds<false, true>{P.lg + ca, 0}, ce - ca, rw, GlobalV{Vin}, pess,
                                       ws, lane, h, &hout);
           if (lane == 0 && hint && hout != h) hint[c] = hout;
           if (best < 0 || (maxi ? q > bq : q < bq)) {
@@ -1222,6 +1238,182 @@ __global__ void __launch_bounds__(32 * NW, MINB) bellman_direct_kernel(StepLaunc
       direct_tile<false>(L, T, k_iter, ws, lane);
   }
   end_of_launch(L, &is_last);
+}
+
+// ---------------------------------------------------------------- small problems
+//
+// One CTA runs all n iterations of a session holding one small problem in a
+// single launch: the model (destinations, bound pairs, column words, hints) and
+// both value buffers are copied into shared memory once, each iteration
+// computes the problem's states from there (warps take states), and the
+// iteration state advances exactly as end_of_launch advances it after every
+// launch of the tiled kernels. The columns run the same exact routines (V read
+// from shared memory), so the words are those of the tiled kernels. This
+// removes the per-iteration launch (a few microseconds each, more than the
+// work of such a problem).
+constexpr int kTinyWarps = 4;
+
+struct TinyLayout {
+  size_t lg, v, rem, sptr, cptr, rows, hint, shift, xoff, fixed, ws, bytes;
+};
+
+__host__ __device__ inline TinyLayout tiny_layout(int32_t n, int32_t m, int32_t nnz, bool f32) {
+  auto up = [](size_t x) { return (x + 15) & ~size_t(15); };
+  TinyLayout t;
+  size_t o = 0;
+  t.lg = o;    o = up(o + (size_t)nnz * (f32 ? sizeof(uint2) : sizeof(ulonglong2)));
+  t.v = o;     o = up(o + 2 * (size_t)n * sizeof(uint64_t));
+  t.rem = o;   o = up(o + (size_t)m * sizeof(uint64_t));
+  t.sptr = o;  o = up(o + (size_t)(n + 1) * sizeof(int32_t));
+  t.cptr = o;  o = up(o + (size_t)(m + 1) * sizeof(int32_t));
+  t.rows = o;  o = up(o + (size_t)nnz * sizeof(int32_t));
+  t.hint = o;  o = up(o + (size_t)m * sizeof(int32_t));
+  t.shift = o; o = up(o + (size_t)m * sizeof(int32_t));
+  t.xoff = o;  o = up(o + (size_t)m * sizeof(int32_t));
+  t.fixed = o; o = up(o + (size_t)n);
+  t.ws = o;    o = up(o + kTinyWarps * sizeof(WarpScratch));
+  t.bytes = o;
+  return t;
+}
+
+template <bool f32>
+__global__ void __launch_bounds__(32 * kTinyWarps, 1) bellman_tiny_kernel(StepLaunch L, int32_t n_iters) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const Problem& P = L.probs[0];
+  const int32_t n = P.n_states;
+  const int32_t m = P.stateptr[n];
+  const int32_t nnz = P.colptr[m];
+  const TinyLayout lay = tiny_layout(n, m, nnz, f32);
+  uint64_t* V0 = reinterpret_cast<uint64_t*>(sm + lay.v);
+  uint64_t* rem = reinterpret_cast<uint64_t*>(sm + lay.rem);
+  int32_t* sptr = reinterpret_cast<int32_t*>(sm + lay.sptr);
+  int32_t* cptr = reinterpret_cast<int32_t*>(sm + lay.cptr);
+  int32_t* rows = reinterpret_cast<int32_t*>(sm + lay.rows);
+  int32_t* hint = reinterpret_cast<int32_t*>(sm + lay.hint);
+  int32_t* shift = reinterpret_cast<int32_t*>(sm + lay.shift);
+  int32_t* xoff = reinterpret_cast<int32_t*>(sm + lay.xoff);
+  uint8_t* fixed = sm + lay.fixed;
+  WarpScratch* ws = reinterpret_cast<WarpScratch*>(sm + lay.ws) + (threadIdx.x >> 5);
+  __shared__ IterState it;
+  __shared__ unsigned long long dmax_b;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  for (int32_t i = tid; i < nnz; i += nt) {
+    rows[i] = P.rowval[i];
+    if (f32)
+      reinterpret_cast<uint2*>(sm + lay.lg)[i] = P.lg32[i];
+    else
+      reinterpret_cast<ulonglong2*>(sm + lay.lg)[i] = P.lg[i];
+  }
+  for (int32_t i = tid; i < n; i += nt) {
+    V0[i] = P.V[0][i];
+    V0[n + i] = P.V[1][i];
+    fixed[i] = P.fixed[i];
+  }
+  for (int32_t i = tid; i <= n; i += nt) sptr[i] = P.stateptr[i];
+  for (int32_t i = tid; i <= m; i += nt) cptr[i] = P.colptr[i];
+  for (int32_t c = tid; c < m; c += nt) {
+    rem[c] = P.rem[c];
+    hint[c] = P.hint ? P.hint[c] : -1;
+    if (f32) {
+      shift[c] = P.shift[c];
+      xoff[c] = P.xoff ? P.xoff[c] : -1;
+    }
+  }
+  if (tid == 0) it = L.its[0];
+  __syncthreads();
+
+  const bool pess = P.pessimistic != 0, maxi = P.maximize != 0;
+  for (int32_t step = 0; step < n_iters; ++step) {
+    if (it.done) break;  // later launches would change nothing
+    const int32_t k_iter = it.iter + 1;
+    const bool active = P.infinite || k_iter <= P.horizon;
+    if (tid == 0) dmax_b = 0;
+    __syncthreads();
+    if (active) {
+      const SharedV Vin{V0 + (size_t)((k_iter - 1) & 1) * n};
+      uint64_t* Vout = V0 + (size_t)(k_iter & 1) * n;
+      unsigned long long dmax = 0;
+      for (int32_t s = warp; s < n; s += kTinyWarps) {
+        if (fixed[s]) continue;  // Eq. 2 fixes reach and avoid states (both buffers hold their values)
+        const int32_t jb = sptr[s], je = sptr[s + 1];
+        uint64_t bq = 0;
+        int32_t best = -1;
+        for (int32_t c = jb; c < je; ++c) {
+          const int32_t ca = cptr[c], ce = cptr[c + 1];
+          const int32_t h = hint[c];
+          int32_t hout;
+          uint64_t q;
+          if (f32 && xoff[c] >= 0)  // correction column: its exact pairs from global memory
+            q = column_q<false, true>(GRows{P.rowval + ca}, Bounds<false, true>{P.lgx + xoff[c], 0}, ce - ca, rem[c],
+                                      Vin, pess, ws, lane, h, &hout);
+          else if (f32)
+            q = column_q<true, false>(rows + ca, Bounds<true>{reinterpret_cast<const uint2*>(sm + lay.lg) + ca,
+                                                              32 - shift[c]},
+                                      ce - ca, rem[c], Vin, pess, ws, lane, h, &hout);
+          else
+            q = column_q<false, false>(rows + ca, Bounds<false>{reinterpret_cast<const ulonglong2*>(sm + lay.lg) + ca, 0},
+                                       ce - ca, rem[c], Vin, pess, ws, lane, h, &hout);
+          if (lane == 0) hint[c] = hout;
+          if (best < 0 || (maxi ? q > bq : q < bq)) {
+            bq = q;
+            best = c - jb;
+          }
+        }
+        const uint64_t vnew = free_state_value(P, s, bq);
+        if (lane == 0) {
+          Vout[s] = vnew;
+          if (P.policy_mode == 1)
+            P.policy[(size_t)(P.horizon - k_iter) * P.n_states + s] = best;
+          else if (P.policy_mode == 2)
+            P.policy[s] = best;
+          if (P.infinite) {
+            const uint64_t vold = Vin.p[s];
+            const uint64_t d = vnew > vold ? vnew - vold : vold - vnew;
+            dmax = d > dmax ? d : dmax;
+          }
+        }
+      }
+      if (lane == 0 && dmax) atomicMax(&dmax_b, dmax);
+    }
+    __syncthreads();
+    if (tid == 0) {  // the iteration state, as end_of_launch advances it
+      const int32_t kq = it.iter + 1;
+      if (!P.infinite && kq > P.horizon) {
+        it.done = 1;
+        it.k_final = it.iter;
+      } else {
+        it.iter = kq;
+        if (P.infinite) {
+          if (dmax_b < P.eps_fix && !P.external_stop) {
+            it.done = 1;
+            it.k_final = kq;
+          } else if (kq >= P.horizon) {
+            it.done = 1;
+            it.k_final = kq;
+            it.noconv = 1;
+          }
+        } else if (kq >= P.horizon) {
+          it.done = 1;
+          it.k_final = kq;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  for (int32_t i = tid; i < n; i += nt) {
+    P.V[0][i] = V0[i];
+    P.V[1][i] = V0[n + i];
+  }
+  if (P.hint)
+    for (int32_t c = tid; c < m; c += nt) P.hint[c] = hint[c];
+  if (tid == 0) {
+    IterState out = it;
+    out.resmax = 0;
+    L.its[0] = out;
+  }
 }
 
 // ---------------------------------------------------------------- wide states
@@ -1752,9 +1944,46 @@ int bellman_grid() {
 
 std::atomic<int> g_stall_producer{0};
 
+cudaError_t launch_bellman_tiny(const StepLaunch& L, int32_t n_iters, bool f32, cudaStream_t st) {
+  static std::atomic<int> configured[64];
+  static std::mutex setup;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!configured[dev].load(std::memory_order_acquire)) {
+    std::lock_guard<std::mutex> lk(setup);
+    if (!configured[dev].load(std::memory_order_relaxed)) {
+      const int most = (int)tiny_layout(kTinyMaxStates, kTinyMaxCols, kTinyMaxEntries, false).bytes;
+      cudaError_t e = cudaFuncSetAttribute(bellman_tiny_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(bellman_tiny_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+      if (e != cudaSuccess) return e;
+      configured[dev].store(1, std::memory_order_release);
+    }
+  }
+  if (n_iters <= 0) return cudaSuccess;
+  const size_t bytes = tiny_layout(L.tiny_states, L.tiny_cols, L.tiny_entries, f32).bytes;
+  if (f32)
+    bellman_tiny_kernel<true><<<1, 32 * kTinyWarps, bytes, st>>>(L, n_iters);
+  else
+    bellman_tiny_kernel<false><<<1, 32 * kTinyWarps, bytes, st>>>(L, n_iters);
+  return cudaGetLastError();
+}
+
 LaunchConfig resolve_launch(const StepLaunch& L, const LaunchConfig* cfg) {
   LaunchConfig r;
   if (cfg) r = *cfg;
+  if (r.kernel == kKernelTiny || (r.kernel == kKernelRule && L.tiny_ok)) {
+    if (L.tiny_ok) {
+      r.kernel = kKernelTiny;
+      r.cta_warps = kTinyWarps;
+      r.ctas_per_sm = 1;
+      if (r.tile_entries <= 0 || r.tile_entries > kTileEntries) r.tile_entries = kTileEntries;
+      if (r.wide_col <= 0) r.wide_col = kWideCol;
+      return r;
+    }
+    r.kernel = kKernelRule;
+  }
   if (r.kernel != kKernelDirect) r.kernel = kKernelRing;
   if (r.kernel == kKernelDirect) {
     r.cta_warps = kDirectWarps;

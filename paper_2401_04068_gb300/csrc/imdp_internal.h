@@ -137,7 +137,10 @@ struct StepControl {
 
 // Launch configuration of the Bellman step (per session; chosen by rule or by
 // the autotuner). Zero fields mean "by rule".
-enum : int32_t { kKernelRule = 0, kKernelRing = 1, kKernelDirect = 2 };
+enum : int32_t { kKernelRule = 0, kKernelRing = 1, kKernelDirect = 2, kKernelTiny = 3 };
+// A session of one problem this small runs all its iterations in one launch of
+// one CTA, with the model and values in shared memory (bellman_tiny_kernel).
+constexpr int32_t kTinyMaxStates = 1024, kTinyMaxCols = 1024, kTinyMaxEntries = 4096;
 constexpr int kDirectWarps = 8;  // warps per CTA of the direct kernel
 struct LaunchConfig {
   int32_t kernel = kKernelRule;  // ring: TMA-fed shared-memory tiles; direct: warps stream tiles from global memory
@@ -184,6 +187,8 @@ struct StepLaunch {
   // with r the largest rank still running.
   const int32_t* rank_of;        // count: rank of each problem
   const int32_t* rank_tile_end;  // count: tiles of ranks 0..r
+  int32_t tiny_ok;     // one small problem (sizes below): the single-CTA kernel may run it
+  int32_t tiny_states, tiny_cols, tiny_entries;
   int32_t grid_total;  // CTAs of both step kernels in this launch (set by the launcher)
   int32_t stall;       // test hook: the producer issues nothing, so every wait runs out
 };
@@ -206,6 +211,9 @@ extern std::atomic<int> g_stall_producer;
 // must follow the same configuration's tile plan.
 cudaError_t launch_bellman_step(const StepLaunch& L, int grid, cudaStream_t st, const SideStream* side = nullptr,
                                 const LaunchConfig* cfg = nullptr);
+// n_iters Bellman iterations of a session's single small problem (L.tiny_ok) in
+// one launch of one CTA.
+cudaError_t launch_bellman_tiny(const StepLaunch& L, int32_t n_iters, bool f32, cudaStream_t st);
 // CTAs of the persistent tiled kernel: one per SM.
 int bellman_grid();
 // The configuration a launch of `L` with `cfg` (nullable) actually uses: kernel,

@@ -268,6 +268,13 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   S->L.count = count;
   S->L.total_states = (int32_t)total;
   S->L.any_infinite = S->any_infinite ? 1 : 0;
+  if (count == 1 && !is_slice(ms[0]) && ms[0]->n_states <= kTinyMaxStates && ms[0]->n_cols <= kTinyMaxCols &&
+      ms[0]->nnz <= kTinyMaxEntries) {
+    S->L.tiny_ok = 1;
+    S->L.tiny_states = ms[0]->n_states;
+    S->L.tiny_cols = ms[0]->n_cols;
+    S->L.tiny_entries = (int32_t)ms[0]->nnz;
+  }
   S->grid = bellman_grid();
   imdp_status r = S->install_plan(tiles, wide, st);
   if (r != IMDP_OK) { delete S; return r; }
@@ -394,6 +401,14 @@ imdp_status Session::step(int32_t n, cudaStream_t st) {
   if (n <= 0) return IMDP_OK;
   TraceRange trace("imdp session step");
   cudaError_t e = cudaSuccess;
+  if (resolve_launch(L, &cfg).kernel == kKernelTiny) {
+    // one small problem: all n iterations in one launch of one CTA
+    e = launch_bellman_tiny(L, n, models[0]->lg32 != nullptr, st);
+    if (e != cudaSuccess) return cuda_status(e, "bellman step");
+    launches += n;
+    launched_since_reset += n;
+    return IMDP_OK;
+  }
   int32_t done = 0;
   if (st != nullptr && n >= kGraphChunk) {
     if (!graph) {

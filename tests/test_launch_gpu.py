@@ -12,7 +12,7 @@ import pytest
 
 import paper_2401_04068_gb300 as g
 from gpu_helpers import TOL_F64, run_oracle
-from workloads import banded_batch, banded_imdp
+from workloads import banded_batch, banded_imdp, random_imdp
 
 pytestmark = pytest.mark.gpu
 
@@ -168,3 +168,85 @@ def test_finished_problems_leave_the_tile_walk(cfg):
     _, oV, _, _, _ = run_oracle(ms[1], horizon=40, reach=ms[1].goal)
     np.testing.assert_allclose(V, oV, rtol=0, atol=TOL_F64)
     sess.close()
+
+
+@pytest.mark.parametrize("case", ["reach", "reach_avoid", "reward", "infinite", "policy", "f32"])
+def test_single_cta_kernel_matches_tiled_kernels(case):
+    # A session of one small problem runs all its iterations in one launch of
+    # one CTA (the rule picks it); the tiled kernels give the same words.
+    m = banded_imdp(120, 3, 120 * 3 * 8 + 120 * 3 + 1, eps=0.1, seed=70)
+    # short columns round finely: a budget this small keeps some of them exact
+    model = g.create_model(m, dtype=g.IMDP_F32, budget=7e-10) if case == "f32" else g.create_model(m)
+    if case == "f32":
+        assert g.imdp_model_exact_columns(model)[0] > 0
+    K = 30
+    okw = dict(horizon=K, reach=m.goal)
+    if case == "reach_avoid":
+        okw.update(property=g.IMDP_REACH_AVOID, avoid=np.setdiff1d(np.arange(0, m.n_states, 17), m.goal),
+                   pessimistic=False)
+    elif case == "reward":
+        okw = dict(property=g.IMDP_REWARD, horizon=K, reward=np.linspace(-1.0, 2.0, m.n_states), discount=0.95,
+                   maximize=False)
+    elif case == "infinite":
+        okw = dict(infinite_time=True, eps=1e-9, horizon=100000, reach=m.goal)
+    spec = g.make_spec(**okw)
+    outs = []
+    for kernel in (g.KERNEL_RULE, g.KERNEL_RING, g.KERNEL_DIRECT):
+        sess = g.imdp_session_create([model], [spec], want_policy=[1] if case == "policy" else None)
+        g.imdp_session_set_launch(sess, kernel=kernel)
+        want = g.KERNEL_TINY if kernel == g.KERNEL_RULE else kernel
+        assert g.imdp_session_get_launch(sess)["kernel"] == want
+        g.imdp_session_run(sess)
+        raw, k = g.imdp_session_checkpoint(sess, 0)
+        pol = None
+        if case == "policy":
+            pol = np.zeros((K, m.n_states), np.int32)
+            g.imdp_session_read(sess, 0, None, None, None, pol)
+        res = np.zeros(m.n_states)
+        g.imdp_session_read(sess, 0, None, None, res, check=False)
+        outs.append((raw, k, pol, res))
+        sess.close()
+    for raw, k, pol, res in outs[1:]:
+        assert k == outs[0][1] and np.array_equal(raw, outs[0][0])
+        assert np.array_equal(res, outs[0][3])
+        if pol is not None:
+            assert np.array_equal(pol, outs[0][2])
+    V = np.zeros(m.n_states)
+    st, oV, ok, _, _ = run_oracle(m, **okw)
+    sess = g.imdp_session_create([model], [spec])
+    g.imdp_session_run(sess)
+    g.imdp_session_read(sess, 0, V)
+    sess.close()
+    tol = TOL_F64 * max(1.0, float(np.max(np.abs(oV))))
+    if case == "f32":
+        tol = K * model.error_bound() + TOL_F64
+    if case == "infinite":
+        tol = 1e-8
+    assert float(np.max(np.abs(V - oV))) <= tol
+
+
+def test_single_cta_kernel_stepwise_and_restore():
+    # step calls of several sizes (one launch each) equal one long run; a
+    # checkpoint taken mid-way resumes there
+    m = random_imdp(40, max_actions=3, seed=71)
+    model = g.create_model(m)
+    spec = g.make_spec(horizon=50, reach=m.goal)
+    a = g.imdp_session_create([model], [spec])
+    g.imdp_session_run(a)
+    ra, ka = g.imdp_session_checkpoint(a, 0)
+    b = g.imdp_session_create([model], [spec])
+    for n in (1, 7, 16, 3):
+        g.imdp_session_step(b, n)
+    raw, k = g.imdp_session_checkpoint(b, 0)
+    assert k == 27
+    c = g.imdp_session_create([model], [spec])
+    g.imdp_session_restore(c, 0, raw, k)
+    g.imdp_session_run(c)
+    g.imdp_session_step(b, 100)  # past the horizon: nothing changes after 50
+    rb, kb = g.imdp_session_checkpoint(b, 0)
+    rc, kc = g.imdp_session_checkpoint(c, 0)
+    assert ka == kb == kc == 50
+    assert np.array_equal(ra, rb)
+    np.testing.assert_allclose(rc.astype(np.float64), ra.astype(np.float64), rtol=0, atol=1e-13 * 2.0 ** 63)
+    for s_ in (a, b, c):
+        s_.close()
