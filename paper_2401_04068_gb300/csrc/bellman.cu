@@ -245,26 +245,27 @@ __device__ __forceinline__ uint64_t warp_excl_scan_sat(uint64_t x, int lane) {
 // iteration (-1: none); the entry that holds it now is returned in *hint_out.
 // Returns q in Q2.62.
 //
-// Loads from global memory: a column's destinations and bounds are read once
-// per pass and streamed (L1 evict-first), the values V_{k-1} are gathered by
-// many columns and kept (L1 evict-last). All of them are read-only during a
-// launch (V_k goes to the other buffer), so the non-coherent path is used. The
+// Loads from global memory: a column's destinations and bounds (default L1
+// policy: a column whose warm start misses is read again by the search, from
+// L1), and the values V_{k-1}, gathered by many columns and kept (L1
+// evict-last). All of them are read-only during a launch (V_k goes to the
+// other buffer), so the non-coherent path is used. The
 // asm is volatile so that the compiler never executes a load speculatively
 // ahead of the bounds test that guards it (entries past a column's end may lie
 // past the end of the array).
 __device__ __forceinline__ int32_t ld_stream_i32(const int32_t* p) {
   int32_t v;
-  asm volatile("ld.global.nc.L1::evict_first.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ ulonglong2 ld_stream_u64x2(const ulonglong2* p) {
   ulonglong2 v;
-  asm volatile("ld.global.nc.L1::evict_first.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p));
+  asm volatile("ld.global.nc.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p));
   return v;
 }
 __device__ __forceinline__ uint2 ld_stream_u32x2(const uint2* p) {
   uint2 v;
-  asm volatile("ld.global.nc.L1::evict_first.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
   return v;
 }
 __device__ __forceinline__ uint64_t ld_value(const uint64_t* p) {
@@ -361,7 +362,9 @@ __device__ __forceinline__ void warm_pass(const typename RowsOf<gmem>::type rows
   }
 }
 
-// The warm pass on 32-bit storage, in 32-bit arithmetic. Values are the high
+// The warm pass on 32-bit storage, in 32-bit arithmetic (unrolled four trips
+// deep: a trip's loads in flight take half the registers of the 64-bit pass's,
+// and the deeper unroll keeps twice as many in flight). Values are the high
 // words vh (Q1.31) of value words whose low words are zero; bounds are the
 // column's mantissas m (value m 2^-(31+s), s = shift_j). Each product vh * m is
 // exact in 64 bits, and (vh * m) >> s equals the 64-bit routines' product
@@ -374,7 +377,7 @@ __device__ __forceinline__ void warm_pass32(const typename RowsOf<gmem>::type ro
                                             int32_t k, const VP V, uint32_t vk, int s, bool pess,
                                             int lane, uint64_t& acc, uint64_t& flt, uint64_t& geq) {
   const int nb = (k + 31) >> 5;
-#pragma unroll 2
+#pragma unroll 4
   for (int it = 0; it < nb; ++it) {
     const int idx = it * 32 + lane;
     const bool ok = idx < k;
