@@ -352,8 +352,7 @@ def run_ours(args, rank, world, local_rank):
     launch_ms = kernel_ms / max(1, launches)  # per launched iteration (includes any past convergence)
     n_tiles, n_wide, wide_entries = g.imdp_session_plan(sess)
     wide_share = wide_entries / max(1, m.nnz)
-    kernel = "bellman_wide_kernel" if wide_share > 0.5 else \
-        ("bellman_direct_kernel" if launch["kernel"] == 2 else "bellman_step_kernel")
+    kernel = "bellman_wide_kernel" if wide_share > 0.5 else KERNEL_NAMES.get(launch["kernel"], "bellman_step_kernel")
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
     traffic = recorded_traffic(args.workload + ("" if args.dtype == "f64" else ":f32"))
     cfg = workload_config(args.workload, m, args.horizon)
@@ -383,7 +382,7 @@ def run_ours(args, rank, world, local_rank):
         # the paper's number is for its query only: pimdp_2, finite K = 200, no policy output
         "vs_baseline": (value / world / PAPER_PIMDP2_RATE)
         if (args.workload == "pimdp2" and args.horizon == 200 and not args.infinite and not args.policy) else None,
-        "dtype": "u64", "data": "synthetic (seeded banded IMDPs shaped like the paper's benchmark table)",
+        "dtype": "u32" if args.dtype == "f32" else "u64", "data": "synthetic (seeded banded IMDPs shaped like the paper's benchmark table)",
         "config": cfg,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
@@ -409,10 +408,15 @@ def f32_budget(args):
     return args.f32_budget if (args.dtype == "f32" and args.f32_budget > 0) else None
 
 
+KERNEL_NAMES = {1: "bellman_step_kernel", 2: "bellman_direct_kernel", 3: "bellman_tiny_kernel",
+                4: "bellman_slice_kernel"}
+
+
 def parse_launch(text: str) -> dict:
-    """'ring[:warps]' or 'direct[:ctas_per_sm[:tile_entries[:wide_col]]]' -> launch fields."""
+    """'ring[:warps]', 'direct[:ctas_per_sm[:tile_entries[:wide_col]]]' or
+    'slice[:ctas_per_sm]' -> launch fields."""
     parts = text.split(":")
-    kind = {"ring": 1, "direct": 2}[parts[0]]
+    kind = {"ring": 1, "direct": 2, "slice": 4}[parts[0]]
     nums = [int(x) for x in parts[1:]]
     if kind == 1:
         keys = ["cta_warps", "tile_entries", "wide_col"]
@@ -522,7 +526,7 @@ def run_uneven(args, rank, world, local_rank):
     out = {
         "metric": METRIC.replace("K=200", "K per problem"), "value": total_units / (elapsed_ms / 1e3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32" if args.dtype == "f32" else "u64",
         "data": "synthetic (seeded banded IMDPs, per-problem shapes and horizons)",
         "config": {"workload": f"uneven_x{n}", "problems": n, "transitions": int(nnz.sum()),
                    "states": int(sum(m.n_states for m in ms)), "horizon": "U{50..500} per problem",
@@ -531,7 +535,7 @@ def run_uneven(args, rank, world, local_rank):
                    "generation_s": round(gen_s, 1), "parallelism": "replicas", "launch": launch},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "bellman_direct_kernel" if launch["kernel"] == 2 else "bellman_step_kernel",
+                     "kernel": KERNEL_NAMES.get(launch["kernel"], "bellman_step_kernel"),
                      "note": "algorithmic bytes of every running problem summed over the step's launches"},
         "clocks": clk, "gpu_launches": int(launches + args.steps), "e2e": None,
     }
@@ -620,7 +624,7 @@ def run_latency(args, rank, world, local_rank):
         "metric": "query latency, one small model (K Bellman iterations per query)", "value": pct(e2e, 50),
         "unit": "ms per query", "n_gpus": world, "steps": n, "warmup": max(args.warmup, 3),
         "ms_per_step": pct(e2e, 50), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u64", "data": "the paper's worked example (Sec. 3.1)" if args.workload == "worked_example"
+        "dtype": "u32" if args.dtype == "f32" else "u64", "data": "the paper's worked example (Sec. 3.1)" if args.workload == "worked_example"
         else "synthetic (seeded banded IMDP shaped like linear_5_states)",
         "config": {"workload": args.workload, "states": int(m.n_states), "columns": ncols, "transitions": nnz,
                    "horizon": K, "query": "maximize pessimistic reachability, finite horizon",
@@ -661,7 +665,8 @@ def run_served(args, rank, world, local_rank):
         g.imdp_server_set_launch(server, **launch)
         launch["chosen_by"] = "explicit"
     # warm-up: one request through the whole path (module load, first graph)
-    w = g.create_model(models_h[0], stream=stream)
+    dtype = g.IMDP_F32 if args.dtype == "f32" else g.IMDP_F64
+    w = g.create_model(models_h[0], dtype=dtype, stream=stream, budget=f32_budget(args))
     tk = g.imdp_server_submit(server, w, g.make_spec(horizon=10, reach=models_h[0].goal))
     assert g.imdp_server_wait(server, tk, 60000.0, np.zeros(models_h[0].n_states)) == g.IMDP_OK
     rng = np.random.default_rng(99 + rank)
@@ -701,7 +706,7 @@ def run_served(args, rank, world, local_rank):
                 f = dev_models[mi] = Future()
         if mine:
             tc = time.perf_counter()
-            f.set_result(g.create_model(models_h[mi], stream=local.stream))
+            f.set_result(g.create_model(models_h[mi], dtype=dtype, stream=local.stream, budget=f32_budget(args)))
             create_s.append(time.perf_counter() - tc)
         return f.result()
 
@@ -747,9 +752,12 @@ def run_served(args, rank, world, local_rank):
         "metric": "served robust value iteration: transition-updates/s and arrival-to-result latency",
         "value": units / span, "unit": UNIT, "n_gpus": world, "steps": n_req, "warmup": 1,
         "ms_per_step": span * 1e3 / n_req, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u64", "data": "synthetic (seeded banded IMDPs, log-uniform shapes)",
+        "dtype": "u32" if args.dtype == "f32" else "u64", "data": "synthetic (seeded banded IMDPs, log-uniform shapes)",
         "config": {"workload": f"served_poisson{int(args.rate)}", "requests": n_req, "rate_per_s": args.rate,
                    "launch": launch,
+                   "storage": ("32-bit + correction, per-iteration budget %g (guaranteed %g at K = 500)"
+                               % (args.f32_budget or 5e-9, 500 * (args.f32_budget or 5e-9)))
+                   if args.dtype == "f32" else "64-bit",
                    "new_models": len(models_h), "client_threads": args.client_threads,
                    "shapes": "states log-U[50,4000], actions U{1..3}, "
                    "window log-U[3,700], K U{100..500}", "server_budget_gb": args.server_budget_gb,
@@ -822,7 +830,7 @@ def run_state_sharded(args, rank, world, local_rank):
     out = {
         "metric": METRIC, "value": units / (elapsed_ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-        "scaling": "strong", "vs_baseline": None, "dtype": "u64",
+        "scaling": "strong", "vs_baseline": None, "dtype": "u32" if args.dtype == "f32" else "u64",
         "data": "synthetic (seeded banded IMDP shaped like the paper's benchmark table)", "config": cfg,
         "clocks": clk, "exchange_bytes_per_step": int(8 * m.n_states * args.horizon) if world > 1 else 0,
     }
@@ -844,7 +852,7 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="storage of the transition bounds")
     ap.add_argument("--f32-budget", type=float, default=0.0,
                     help="32-bit storage: per-iteration error budget of the correction stage (0: library default)")
-    ap.add_argument("--launch", default="", help="explicit launch configuration, e.g. ring:24 or direct:4:1024")
+    ap.add_argument("--launch", default="", help="explicit launch configuration, e.g. ring:24, direct:4:1024 or slice:4")
     ap.add_argument("--tune", default="cache", choices=["cache", "fresh", "off"],
                     help="autotuner: cached choice (timing only shapes missing from the cache), time now, or rule")
     ap.add_argument("--tune-cache", default="", help="autotuner cache file (default: the package's GB300 table)")

@@ -188,7 +188,8 @@ IMDP_API imdp_status imdp_model_plan(const imdp_model* m, int32_t* n_tiles, int3
 
 /* TEST-ONLY hook for failure detection (no counterpart in the paper; never
  * call it in production code). While `on` is nonzero, step launches of the
- * tiled kernel issue no tile copies: every consumer wait runs into its bound
+ * ring kernel (launch configuration kernel 1) issue no tile copies: every
+ * consumer wait runs into its bound
  * (about 2 s), the kernel records the error and returns, and the next read of
  * the session reports IMDP_ETIMEOUT; the CUDA context stays usable. The switch
  * is process-wide; imdp_session_reset turns it off again (and drops the
@@ -229,11 +230,14 @@ IMDP_API imdp_status imdp_value_iteration_batch(imdp_model* const* models, const
  * start-up and may not allocate afterwards: a controller re-planning every cycle
  * under a fixed memory budget, or code whose device memory belongs to another
  * framework's allocator. Instead of per-call buffers it uses one fixed scratch
- * array compiled into the library (about 2.7 MB, held by every GPU that loads
+ * array compiled into the library (about 3.7 MB, held by every GPU that loads
  * the library until the process exits).
  *   m, spec   as for imdp_value_iteration (reach / reach-avoid properties);
  *             at most 131072 states and 131072 reach + avoid indices, else
- *             IMDP_EINVAL with a message naming the limit
+ *             IMDP_EINVAL with a message naming the limit; a model of at most
+ *             262144 columns keeps its threshold hints from one iteration to
+ *             the next as a session does (a larger one searches every column
+ *             every iteration: slower, equal up to the products' truncation)
  *   V_out     double[n_states], DEVICE memory on the model's device (current)
  *   k_out     (host, nullable) iterations performed
  * The first call on a device looks up the scratch array's device address; make
@@ -294,15 +298,26 @@ IMDP_API void imdp_session_destroy(imdp_session* s);
  *                 one CTA keeps the model and its values in shared memory and
  *                 runs every iteration of a step call in one launch (sessions of
  *                 one problem with at most 1024 states, 1024 columns and 4096
- *                 transitions that is not a slice; IMDP_EINVAL otherwise)
+ *                 transitions that is not a slice; IMDP_EINVAL otherwise); 4 slice:
+ *                 one lane per column over a second, interleaved copy of every
+ *                 model (its "slice layout": windows of whole states of at most
+ *                 256 columns, ordered by length and dealt to slices of 32
+ *                 columns, entry t of a slice's 32 columns stored contiguously).
+ *                 The layout is built on the device when a session first selects
+ *                 this kernel (this waits for `stream`); it stays with the model
+ *                 until imdp_model_destroy and takes about 1.06 times the
+ *                 model's transition storage. IMDP_ENOMEM when it does not fit.
  *   cta_warps     ring: 16 or 24 warps per CTA (24 only without wide states; rule:
- *                 24 when the tiles hold 16 or more columns on average); direct: 8
- *   ctas_per_sm   direct: 3 or 4 (rule 4); ring: 1
+ *                 24 when the tiles hold 16 or more columns on average); direct
+ *                 and slice: 8
+ *   ctas_per_sm   direct and slice: 3 or 4 (rule 4); ring: 1
  *   tile_entries  tile plan: at most this many transitions per tile, 1..3072
- *                 (rule 3072; a single state may exceed a smaller limit)
+ *                 (rule 3072; a single state may exceed a smaller limit; the
+ *                 slice kernel has no tile plan and ignores it)
  *   wide_col      a state with a column of this many transitions or more (or
  *                 more than 3072 transitions in all) runs in the block-wide
- *                 kernel (rule 1280)
+ *                 kernel (rule 1280; ignored by the slice kernel, whose lanes run
+ *                 columns of any length)
  */
 typedef struct {
   int32_t kernel;
@@ -319,8 +334,9 @@ IMDP_API imdp_status imdp_session_set_launch(imdp_session* s, const imdp_launch_
  * the rule where the set configuration left it open. */
 IMDP_API imdp_status imdp_session_get_launch(const imdp_session* s, imdp_launch_config* cfg);
 /* The session's current tile plan (it follows the launch configuration's
- * tile_entries and wide_col): tiles streamed by the tiled kernels, wide states
- * and their transitions. Any output may be NULL. */
+ * tile_entries and wide_col): tiles streamed by the tiled kernels (windows of
+ * the slice layout for the slice kernel), wide states and their transitions.
+ * Any output may be NULL. */
 IMDP_API imdp_status imdp_session_plan(const imdp_session* s, int32_t* n_tiles, int32_t* n_wide,
                                        int64_t* wide_entries);
 /*

@@ -52,7 +52,7 @@ class imdp_launch_config(C.Structure):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
-KERNEL_RULE, KERNEL_RING, KERNEL_DIRECT, KERNEL_TINY = 0, 1, 2, 3
+KERNEL_RULE, KERNEL_RING, KERNEL_DIRECT, KERNEL_TINY, KERNEL_SLICE = 0, 1, 2, 3, 4
 
 
 class ImdpError(RuntimeError):

@@ -177,7 +177,7 @@ extern "C" {
 IMDP_API imdp_status imdp_session_set_launch(imdp_session* s, const imdp_launch_config* cfg, void* stream) {
   set_error("");
   if (!s || !s->s || !cfg) { set_error("NULL session or configuration"); return IMDP_EINVAL; }
-  if (cfg->kernel < 0 || cfg->kernel > 3 || cfg->tile_entries < 0 || cfg->wide_col < 0) {
+  if (cfg->kernel < 0 || cfg->kernel > 4 || cfg->tile_entries < 0 || cfg->wide_col < 0) {
     set_error("bad launch configuration");
     return IMDP_EINVAL;
   }
@@ -253,6 +253,8 @@ IMDP_API imdp_status imdp_session_autotune(imdp_session* s, int32_t iters, const
     add(kKernelDirect, kDirectWarps, 4, kTileEntries, kWideCol);
     add(kKernelDirect, kDirectWarps, 3, kTileEntries, kWideCol);
     add(kKernelDirect, kDirectWarps, 4, 1024, kWideCol);
+    add(kKernelSlice, kSliceWarps, 4, kTileEntries, kWideCol);
+    add(kKernelSlice, kSliceWarps, 3, kTileEntries, kWideCol);
     bool have = false;
     for (const LaunchConfig& c : cands) {
       double ms = 0.0;
@@ -264,7 +266,7 @@ IMDP_API imdp_status imdp_session_autotune(imdp_session* s, int32_t iters, const
       }
     }
     // stage 2: the wide-state threshold, for models with long columns
-    if (r == IMDP_OK && max_col >= 640 && best.kernel != kKernelTiny) {
+    if (r == IMDP_OK && max_col >= 640 && best.kernel != kKernelTiny && best.kernel != kKernelSlice) {
       for (int32_t wc : {640, 2560, 1 << 30}) {
         LaunchConfig c = best;
         c.wide_col = wc;

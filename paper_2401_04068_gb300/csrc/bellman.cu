@@ -249,10 +249,14 @@ __device__ __forceinline__ uint64_t warp_excl_scan_sat(uint64_t x, int lane) {
 // policy: a column whose warm start misses is read again by the search, from
 // L1), and the values V_{k-1}, gathered by many columns and kept (L1
 // evict-last). All of them are read-only during a launch (V_k goes to the
-// other buffer), so the non-coherent path is used. The
-// asm is volatile so that the compiler never executes a load speculatively
-// ahead of the bounds test that guards it (entries past a column's end may lie
-// past the end of the array).
+// other buffer), so the non-coherent path is used. A destination or bound load
+// guarded by a bounds test in C++ is volatile asm, so that the compiler never
+// executes it speculatively ahead of the test (entries past a column's end may
+// lie past the end of the array). The gathers of V always read a valid state,
+// and the predicated loads below carry their guard inside the asm: those are
+// plain asm, which the compiler may schedule freely. (Volatile asm keeps its
+// program order, so a volatile gather would hold every later load behind the
+// load its address waits for.)
 __device__ __forceinline__ int32_t ld_stream_i32(const int32_t* p) {
   int32_t v;
   asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
@@ -270,45 +274,106 @@ __device__ __forceinline__ uint2 ld_stream_u32x2(const uint2* p) {
 }
 __device__ __forceinline__ uint64_t ld_value(const uint64_t* p) {
   uint64_t v;
-  asm volatile("ld.global.nc.L1::evict_last.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  asm("ld.global.nc.L1::evict_last.u64 %0, [%1];" : "=l"(v) : "l"(p));
   return v;
 }
 // High 32 bits of a value word (the whole value of a problem on 32-bit
 // storage, whose values keep their low 32 bits zero).
 __device__ __forceinline__ uint32_t ld_value_hi(const uint64_t* p) {
   uint32_t v;
-  asm volatile("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(v) : "l"(reinterpret_cast<const uint32_t*>(p) + 1));
+  asm("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(v) : "l"(reinterpret_cast<const uint32_t*>(p) + 1));
   return v;
 }
 
-// Destinations of one column in global memory (streamed loads); in shared
-// memory a plain pointer serves.
+// The same loads under a predicate: a lane with `ok` false issues no memory
+// request and gets zeros (the slice kernel's lanes past their column's end).
+// Results come back in 32-bit registers and are assembled after the asm.
+__device__ __forceinline__ int32_t ld_stream_i32_if(const int32_t* p, bool ok) {
+  int32_t v;
+  asm(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\tmov.b32 %0, 0;\n\t@q ld.global.nc.s32 %0, [%1];\n\t}"
+      : "=r"(v)
+      : "l"(p), "r"((int)ok));
+  return v;
+}
+__device__ __forceinline__ ulonglong2 ld_stream_u64x2_if(const ulonglong2* p, bool ok) {
+  uint32_t a, b, c, d;
+  asm(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\tmov.b32 %0, 0;\n\tmov.b32 %1, 0;\n\tmov.b32 %2, 0;\n\t"
+      "mov.b32 %3, 0;\n\t@q ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];\n\t}"
+      : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+      : "l"(p), "r"((int)ok));
+  return make_ulonglong2(((uint64_t)b << 32) | a, ((uint64_t)d << 32) | c);
+}
+__device__ __forceinline__ uint2 ld_stream_u32x2_if(const uint2* p, bool ok) {
+  uint32_t a, b;
+  asm(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\tmov.b32 %0, 0;\n\tmov.b32 %1, 0;\n\t"
+      "@q ld.global.nc.v2.u32 {%0, %1}, [%2];\n\t}"
+      : "=r"(a), "=r"(b)
+      : "l"(p), "r"((int)ok));
+  return make_uint2(a, b);
+}
+__device__ __forceinline__ uint64_t ld_value_if(const uint64_t* p, bool ok) {
+  uint32_t a, b;
+  asm(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\tmov.b32 %0, 0;\n\tmov.b32 %1, 0;\n\t"
+      "@q ld.global.nc.L1::evict_last.v2.u32 {%0, %1}, [%2];\n\t}"
+      : "=r"(a), "=r"(b)
+      : "l"(p), "r"((int)ok));
+  return ((uint64_t)b << 32) | a;
+}
+__device__ __forceinline__ uint32_t ld_value_hi_if(const uint64_t* p, bool ok) {
+  uint32_t v;
+  asm(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\tmov.b32 %0, 0;\n\t"
+      "@q ld.global.nc.L1::evict_last.u32 %0, [%1];\n\t}"
+      : "=r"(v)
+      : "l"(reinterpret_cast<const uint32_t*>(p) + 1), "r"((int)ok));
+  return v;
+}
+
+// Where the column routines read a column's destinations and bounds (`gmem`):
+// 0 shared memory (a plain pointer), 1 contiguous in global memory (streamed
+// loads), 2 one column of a slice of the slice layout, whose entry idx sits
+// 32 idx slots after its first (streamed loads).
+constexpr int kSliceStride = 32;
 struct GRows {
   const int32_t* p;
   __device__ __forceinline__ int32_t operator[](int idx) const { return ld_stream_i32(p + idx); }
 };
-template <bool gmem>
+struct SRows {
+  const int32_t* p;
+  __device__ __forceinline__ int32_t operator[](int idx) const {
+    return ld_stream_i32(p + (size_t)idx * kSliceStride);
+  }
+};
+template <int gmem>
 struct RowsOf {
   typedef const int32_t* type;
 };
 template <>
-struct RowsOf<true> {
+struct RowsOf<1> {
   typedef GRows type;
+};
+template <>
+struct RowsOf<2> {
+  typedef SRows type;
 };
 
 // Bounds of one column as {lower, gap} in Q1.63, from 64-bit storage or from
-// 32-bit mantissas shifted up by `down` = 32 - shift_j; `gmem`: the pairs are
-// in global memory (streamed loads), else in shared memory.
-template <bool f32, bool gmem = false>
+// 32-bit mantissas shifted up by `down` = 32 - shift_j; read as `gmem` says.
+template <bool f32, int gmem = 0>
 struct Bounds {
   const void* p;
   int down;
   __device__ __forceinline__ ulonglong2 operator[](int idx) const {
+    const size_t at = gmem == 2 ? (size_t)idx * kSliceStride : (size_t)idx;
     if (f32) {
-      const uint2 m = gmem ? ld_stream_u32x2(static_cast<const uint2*>(p) + idx) : static_cast<const uint2*>(p)[idx];
+      const uint2 m = gmem ? ld_stream_u32x2(static_cast<const uint2*>(p) + at) : static_cast<const uint2*>(p)[at];
       return make_ulonglong2((uint64_t)m.x << down, (uint64_t)m.y << down);
     }
-    return gmem ? ld_stream_u64x2(static_cast<const ulonglong2*>(p) + idx) : static_cast<const ulonglong2*>(p)[idx];
+    return gmem ? ld_stream_u64x2(static_cast<const ulonglong2*>(p) + at) : static_cast<const ulonglong2*>(p)[at];
   }
 };
 
@@ -334,7 +399,7 @@ struct SharedV {
 // and contribute zero. With `carry` the per-lane gap sums count their wraps and
 // saturate; without it the column is narrow (all its gaps add up to < 2^64), so
 // no sum can wrap.
-template <bool carry, bool f32, bool gmem, class VP>
+template <bool carry, bool f32, int gmem, class VP>
 __device__ __forceinline__ void warm_pass(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k,
                                           const VP V, uint64_t vk, bool pess, int lane,
                                           uint64_t& acc, uint64_t& flt, uint64_t& geq) {
@@ -372,7 +437,7 @@ __device__ __forceinline__ void warm_pass(const typename RowsOf<gmem>::type rows
 // and the same decisions from its gap sums (kept in mantissa units, where no
 // sum can wrap), as warm_pass on the widened bounds: one 32x32 multiply, a
 // shift and a 64-bit add per entry instead of a 64x64 multiply-high.
-template <bool gmem, class VP>
+template <int gmem, class VP>
 __device__ __forceinline__ void warm_pass32(const typename RowsOf<gmem>::type rows, const uint2* __restrict__ m,
                                             int32_t k, const VP V, uint32_t vk, int s, bool pess,
                                             int lane, uint64_t& acc, uint64_t& flt, uint64_t& geq) {
@@ -421,7 +486,7 @@ struct WarmMiss {
   bool valid;
 };
 
-template <bool f32, bool gmem, class VP>
+template <bool f32, int gmem, class VP>
 __device__ __forceinline__ bool column_warm(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem_word,
                                             const VP V, bool pess, int lane, int32_t hint,
                                             uint64_t* q, WarmMiss* miss) {
@@ -483,7 +548,7 @@ __device__ __forceinline__ bool column_warm(const typename RowsOf<gmem>::type ro
 //   above: F(< kappa+) = F(<= kappa), holds when F(<= kappa) + G >= rem;
 // and q is the warm formula at the new key, to the bit. Returns false when the
 // threshold moved further (or a sum is not exact), leaving the full search.
-template <bool f32, bool gmem, class VP>
+template <bool f32, int gmem, class VP>
 __device__ __forceinline__ bool column_neighbor(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem,
                                                 const VP V, bool pess, int lane,
                                                 const WarmMiss& w, uint64_t* q, int32_t* hint_out) {
@@ -542,7 +607,7 @@ __device__ __forceinline__ bool column_neighbor(const typename RowsOf<gmem>::typ
 
 // Threshold search over a column with rem > 0 (the warm start failed or had no
 // hint). Returns q in Q2.62 and the threshold entry in *hint_out.
-template <bool f32, bool gmem, class VP>
+template <bool f32, int gmem, class VP>
 __device__ uint64_t column_search(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem_word,
                                   const VP V, bool pess, WarpScratch* ws, int lane,
                                   int32_t* hint_out) {
@@ -714,7 +779,7 @@ __device__ uint64_t column_search(const typename RowsOf<gmem>::type rows, const 
 }
 
 // One column, warm start first: q in Q2.62, the threshold entry in *hint_out.
-template <bool f32, bool gmem, class VP>
+template <bool f32, int gmem, class VP>
 __device__ uint64_t column_q(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k, uint64_t rem_word,
                              const VP V, bool pess, WarpScratch* ws, int lane, int32_t hint,
                              int32_t* hint_out) {
@@ -1239,6 +1304,280 @@ __global__ void __launch_bounds__(32 * NW, MINB) bellman_direct_kernel(StepLaunc
       direct_tile<true>(L, T, k_iter, ws, lane);
     else
       direct_tile<false>(L, T, k_iter, ws, lane);
+  }
+  end_of_launch(L, &is_last);
+}
+
+// ---------------------------------------------------------------- slice kernel
+//
+// The same Bellman step over the slice layout (one lane per column): every warp
+// takes the next slice (atomic counter) and each lane runs the warm start of
+// the O-maximization (Sec. 4) for its own column, sequentially over the
+// column's entries. The warp's loads of entry t of its 32 columns are one
+// contiguous run, and the sums a column needs stay in its lane, so a column
+// costs no warp reduction and no per-column bookkeeping; in the tiled kernels
+// these cost more issue slots than the entries themselves when columns are
+// short. Columns whose warm start fails (or that have no hint yet), and the
+// exact columns of 32-bit storage, then go through the exact neighbour check
+// and threshold search one at a time with the whole warp, reading the column
+// through the slice layout's stride (from L2: the warp has just streamed it).
+// Each column's q goes to a per-column buffer; the warp that completes the last
+// slice of a window (whole states) finishes the window's states. Every step of
+// a column is the routine the other kernels run, so the words are theirs.
+
+// One lane's warm pass over its column on 64-bit storage: entry t at rows[32 t],
+// lg[32 t]; `len` trips (the slice's longest column), loads off past k. The sums
+// of warm_pass; with `carry`, gap sums that pass 2^64 saturate.
+// Trips are taken kLaneGroup at a time and software-pipelined: the next
+// group's destination and bound loads are issued before this group's gathers
+// and arithmetic, so each lane keeps two groups of streamed loads in flight.
+constexpr int kLaneGroup = 4;
+template <bool carry>
+__device__ __forceinline__ void lane_pass64(const int32_t* rows, const ulonglong2* lg, int32_t len, int32_t k,
+                                            const uint64_t* __restrict__ V, uint64_t vk, bool pess, uint64_t& acc,
+                                            uint64_t& flt, uint64_t& geq) {
+  uint32_t fc = 0, gc = 0;
+  int32_t r[kLaneGroup];
+  ulonglong2 b[kLaneGroup];
+#pragma unroll
+  for (int u = 0; u < kLaneGroup; ++u) {
+    r[u] = ld_stream_i32_if(rows + (size_t)u * kSliceStride, u < k);
+    b[u] = ld_stream_u64x2_if(lg + (size_t)u * kSliceStride, u < k);
+  }
+  for (int32_t t0 = 0; t0 < len; t0 += kLaneGroup) {
+    uint64_t v[kLaneGroup];
+#pragma unroll
+    for (int u = 0; u < kLaneGroup; ++u) v[u] = ld_value_if(V + r[u], t0 + u < k);
+    int32_t rn[kLaneGroup];
+    ulonglong2 bn[kLaneGroup];
+#pragma unroll
+    for (int u = 0; u < kLaneGroup; ++u) {
+      const int32_t t = t0 + kLaneGroup + u;
+      rn[u] = ld_stream_i32_if(rows + (size_t)t * kSliceStride, t < k);
+      bn[u] = ld_stream_u64x2_if(lg + (size_t)t * kSliceStride, t < k);
+    }
+#pragma unroll
+    for (int u = 0; u < kLaneGroup; ++u) {
+      const bool below = pess ? (v[u] < vk) : (v[u] > vk);
+      const uint64_t gb = below ? b[u].y : 0ull, ge = v[u] == vk ? b[u].y : 0ull;
+      acc += __umul64hi(v[u], b[u].x + gb);
+      flt += gb;
+      geq += ge;
+      if (carry) {
+        fc += flt < gb ? 1u : 0u;
+        gc += geq < ge ? 1u : 0u;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kLaneGroup; ++u) {
+      r[u] = rn[u];
+      b[u] = bn[u];
+    }
+  }
+  if (carry) {
+    flt = fc ? ~0ull : flt;
+    geq = gc ? ~0ull : geq;
+  }
+}
+
+// The same on 32-bit storage, in 32-bit arithmetic: the sums of warm_pass32.
+__device__ __forceinline__ void lane_pass32(const int32_t* rows, const uint2* m, int32_t len, int32_t k,
+                                            const uint64_t* __restrict__ V, uint32_t vk, int s, bool pess,
+                                            uint64_t& acc, uint64_t& flt, uint64_t& geq) {
+  int32_t r[kLaneGroup];
+  uint2 b[kLaneGroup];
+#pragma unroll
+  for (int u = 0; u < kLaneGroup; ++u) {
+    r[u] = ld_stream_i32_if(rows + (size_t)u * kSliceStride, u < k);
+    b[u] = ld_stream_u32x2_if(m + (size_t)u * kSliceStride, u < k);
+  }
+  for (int32_t t0 = 0; t0 < len; t0 += kLaneGroup) {
+    uint32_t v[kLaneGroup];
+#pragma unroll
+    for (int u = 0; u < kLaneGroup; ++u) v[u] = ld_value_hi_if(V + r[u], t0 + u < k);
+    int32_t rn[kLaneGroup];
+    uint2 bn[kLaneGroup];
+#pragma unroll
+    for (int u = 0; u < kLaneGroup; ++u) {
+      const int32_t t = t0 + kLaneGroup + u;
+      rn[u] = ld_stream_i32_if(rows + (size_t)t * kSliceStride, t < k);
+      bn[u] = ld_stream_u32x2_if(m + (size_t)t * kSliceStride, t < k);
+    }
+#pragma unroll
+    for (int u = 0; u < kLaneGroup; ++u) {
+      const bool below = pess ? (v[u] < vk) : (v[u] > vk);
+      const uint32_t g = below ? b[u].y : 0u;
+      acc += ((uint64_t)v[u] * (uint64_t)(b[u].x + g)) >> s;
+      flt += g;
+      geq += v[u] == vk ? b[u].y : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kLaneGroup; ++u) {
+      r[u] = rn[u];
+      b[u] = bn[u];
+    }
+  }
+}
+
+// One slice g of window (tile) t: q of its columns into P.qcol, hints updated;
+// the warp that completes the window finishes its states.
+template <bool f32>
+__device__ void slice_run(const StepLaunch& L, const Problem& P, const Tile& T, int32_t t, int32_t g, int32_t k_iter,
+                          WarpScratch* ws, int lane) {
+  const uint64_t* __restrict__ Vin = P.V[(k_iter - 1) & 1];
+  const bool pess = P.pessimistic != 0;
+  const SliceMeta sm = P.sl_meta[g];
+  const int2 sl = P.sl_slot[(size_t)g * 32 + lane];
+  const int32_t c = sl.x, k = sl.y;
+  uint64_t rem_word = 0;
+  int32_t h = -1, sh = 0, xo = -1;
+  if (c >= 0) {
+    rem_word = __ldg(P.rem + c);
+    h = P.hint ? P.hint[c] : -1;
+    if (f32) {
+      sh = __ldg(P.shift + c);
+      xo = P.xoff ? __ldg(P.xoff + c) : -1;
+    }
+  }
+  // hint -2 - i: entry i, and the column's threshold is moving (no neighbour check)
+  const int32_t entry = h <= -2 ? -2 - h : h;
+  const uint64_t rem = rem_of(rem_word);
+  const int32_t* rows = P.sl_rows + sm.off + lane;
+  // lanes that run the warm start: rem = 0 (every entry at its lower bound), or a hint
+  const bool warm = c >= 0 && xo < 0 && (rem == 0 || (entry >= 0 && entry < k));
+  const int32_t kk = warm ? k : 0;
+  const int32_t len = (int32_t)__reduce_max_sync(kFull, (unsigned)kk);  // trips any lane needs
+  uint64_t acc = 0, flt = 0, geq = 0, q = 0;
+  int32_t hout = h;
+  bool done = false;
+  WarmMiss miss;
+  miss.valid = false;
+  if (f32) {
+    const uint2* lg = static_cast<const uint2*>(P.sl_lg) + sm.off + lane;
+    // rem = 0: a key no value passes, so every entry keeps its lower bound
+    uint32_t vk = pess ? 0u : 0xffffffffu;
+    if (warm && rem != 0) vk = ld_value_hi(Vin + ld_stream_i32(rows + (size_t)entry * kSliceStride));
+    lane_pass32(rows, lg, len, kk, Vin, vk, sh, pess, acc, flt, geq);
+    if (warm) {
+      const int down = 32 - sh;
+      const uint64_t rem_m = rem >> down;  // exact: rem is a multiple of 2^down
+      if (rem == 0) {
+        q = acc;
+        done = true;
+      } else if (flt < rem_m && rem_m - flt <= geq) {
+        q = acc + mul_shr(vk, rem_m - flt, sh);
+        done = true;
+      } else {
+        miss = WarmMiss{(uint64_t)vk << 32, acc, shl_sat(flt, down), shl_sat(geq, down), true};
+      }
+    }
+  } else {
+    const ulonglong2* lg = static_cast<const ulonglong2*>(P.sl_lg) + sm.off + lane;
+    uint64_t vk = pess ? 0ull : ~0ull;
+    if (warm && rem != 0) vk = ld_value(Vin + ld_stream_i32(rows + (size_t)entry * kSliceStride));
+    // narrow columns (every gap sum < 2^64) need no saturation
+    if (__all_sync(kFull, !warm || rem == 0 || narrow_of(rem_word)))
+      lane_pass64<false>(rows, lg, len, kk, Vin, vk, pess, acc, flt, geq);
+    else
+      lane_pass64<true>(rows, lg, len, kk, Vin, vk, pess, acc, flt, geq);
+    if (warm) {
+      if (rem == 0) {
+        q = acc;
+        done = true;
+      } else if (flt < rem && rem - flt <= geq) {
+        q = acc + __umul64hi(vk, rem - flt);
+        done = true;
+      } else {
+        miss = WarmMiss{vk, acc, flt, geq, true};
+      }
+    }
+  }
+  if (done) hout = entry;
+  // the rest, one column at a time with the whole warp
+  unsigned need = __ballot_sync(kFull, c >= 0 && !done);
+  while (need) {
+    const int src = __ffs(need) - 1;
+    need &= need - 1;
+    const int32_t cs = __shfl_sync(kFull, c, src), ks = __shfl_sync(kFull, k, src);
+    const int32_t hs = __shfl_sync(kFull, h, src);
+    const uint64_t rws = __shfl_sync(kFull, rem_word, src);
+    const int32_t xs = f32 ? __shfl_sync(kFull, xo, src) : -1;
+    uint64_t qq;
+    int32_t ho;
+    const int32_t ca = __ldg(P.colptr + cs);
+    if (f32 && xs >= 0) {
+      // a correction column (no entries in the slice arrays): its exact bounds
+      const int32_t ce = __ldg(P.colptr + cs + 1);
+      qq = column_q<false, 1>(GRows{P.rowval + ca}, Bounds<false, 1>{P.lgx + xs, 0}, ce - ca, rws, GlobalV{Vin}, pess,
+                              ws, lane, hs, &ho);
+    } else {
+      WarmMiss w;
+      w.valid = __shfl_sync(kFull, miss.valid ? 1 : 0, src) != 0;
+      w.vk = __shfl_sync(kFull, miss.vk, src);
+      w.acc = __shfl_sync(kFull, miss.acc, src);
+      w.flt = __shfl_sync(kFull, miss.flt, src);
+      w.geq = __shfl_sync(kFull, miss.geq, src);
+      // the column's CSC copy: contiguous, so the passes below are coalesced
+      const GRows rs{P.rowval + ca};
+      const void* bp = f32 ? static_cast<const void*>(P.lg32 + ca) : static_cast<const void*>(P.lg + ca);
+      const Bounds<f32, 1> bs{bp, f32 ? 32 - __shfl_sync(kFull, sh, src) : 0};
+      const bool nb = w.valid && hs > -2 &&
+                      column_neighbor<f32, 1>(rs, bs, ks, rem_of(rws), GlobalV{Vin}, pess, lane, w, &qq, &ho);
+      if (!nb) {
+        int32_t found;
+        qq = column_search<f32, 1>(rs, bs, ks, rws, GlobalV{Vin}, pess, ws, lane, &found);
+        ho = found >= 0 ? -2 - found : -1;
+      }
+    }
+    if (lane == src) {
+      q = qq;
+      hout = ho;
+    }
+  }
+  if (c >= 0) {
+    P.qcol[c] = q;
+    if (P.hint && hout != h) P.hint[c] = hout;
+  }
+  // count the slice; the warp that completes the window finishes its states
+  __threadfence();
+  __syncwarp();
+  unsigned prev = 0;
+  if (lane == 0) prev = atomicAdd(&L.win_cnt[t], 1u);
+  prev = __shfl_sync(kFull, prev, 0);
+  if (prev + 1 == (unsigned)(T.x1 - T.x0)) {
+    __threadfence();
+    const unsigned long long* qc = reinterpret_cast<const unsigned long long*>(P.qcol);
+    tile_epilogue(L, P, T, k_iter, lane, [&](int32_t s) { return (uint8_t)__ldg(P.fixed + s); },
+                  [&](int32_t s, uint64_t* bq, int32_t* bb) {
+                    const int32_t jb = __ldg(P.stateptr + s), je = __ldg(P.stateptr + s + 1);
+                    best_action(P, jb, je, [&](int32_t jj) { return (uint64_t)__ldcg(qc + jj); }, bq, bb);
+                  });
+    if (lane == 0) L.win_cnt[t] = 0;  // for the next launch
+  }
+}
+
+template <int NW, int MINB>
+__global__ void __launch_bounds__(32 * NW, MINB) bellman_slice_kernel(StepLaunch L) {
+  __shared__ WarpScratch ws_all[NW];
+  __shared__ int is_last;
+  const int lane = threadIdx.x & 31;
+  WarpScratch* ws = &ws_all[threadIdx.x >> 5];
+  const int32_t nt = tiles_to_visit(L);
+  const int32_t ni = nt <= 0 ? 0 : (nt >= L.n_tiles ? L.n_items : L.tile_item_end[nt - 1]);
+  for (;;) {
+    int32_t i = 0;
+    if (lane == 0) i = (int32_t)atomicAdd(&L.ctl->tile_next, 1u);
+    i = __shfl_sync(kFull, i, 0);
+    if (i >= ni) break;
+    const int2 it = L.items[i];
+    const Tile T = L.tiles[it.x];
+    int32_t k_iter;
+    if (!problem_active(L, T.p, &k_iter)) continue;
+    const Problem& P = L.probs[T.p];
+    if (P.lg32)
+      slice_run<true>(L, P, T, it.x, it.y, k_iter, ws, lane);
+    else
+      slice_run<false>(L, P, T, it.x, it.y, k_iter, ws, lane);
   }
   end_of_launch(L, &is_last);
 }
@@ -1987,6 +2326,13 @@ LaunchConfig resolve_launch(const StepLaunch& L, const LaunchConfig* cfg) {
     }
     r.kernel = kKernelRule;
   }
+  if (r.kernel == kKernelSlice) {
+    r.cta_warps = kSliceWarps;
+    r.ctas_per_sm = r.ctas_per_sm == 3 ? 3 : 4;
+    r.tile_entries = kTileEntries;  // no tile plan: windows of the slice layout
+    r.wide_col = kWideCol;
+    return r;
+  }
   if (r.kernel != kKernelDirect) r.kernel = kKernelRing;
   if (r.kernel == kKernelDirect) {
     r.cta_warps = kDirectWarps;
@@ -2042,10 +2388,15 @@ cudaError_t launch_bellman_step(const StepLaunch& L0, int grid, cudaStream_t st,
   const bool short_cols = kind == kKernelRing && rc.cta_warps == kConsumersShort + 1;
   const int wg = L.n_wide > 0 ? std::min(L.n_wide, wide_blocks[dev]) : 0;
   // one CTA still takes part in the end-of-launch ticket when there are no tiles
-  const int mg = L.n_tiles <= 0 ? 1 : (kind == kKernelDirect ? grid * direct_per_sm : grid);
+  const int mg = L.n_tiles <= 0 ? 1 : ((kind == kKernelDirect || kind == kKernelSlice) ? grid * direct_per_sm : grid);
   L.grid_total = mg + wg;
   const auto tiled = [&](cudaStream_t s) {
-    if (kind == kKernelDirect) {
+    if (kind == kKernelSlice) {
+      if (direct_per_sm == 3)
+        bellman_slice_kernel<kSliceWarps, 3><<<mg, 32 * kSliceWarps, 0, s>>>(L);
+      else
+        bellman_slice_kernel<kSliceWarps, 4><<<mg, 32 * kSliceWarps, 0, s>>>(L);
+    } else if (kind == kKernelDirect) {
       if (direct_per_sm == 3)
         bellman_direct_kernel<kDirectWarps, 3><<<mg, 32 * kDirectWarps, 0, s>>>(L);
       else

@@ -14,6 +14,7 @@
 #include <cstdint>
 #include <string>
 #include <atomic>
+#include <mutex>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -51,6 +52,37 @@ struct Tile {
   int32_t x0, x1; // 32-bit storage: the tile's correction entries, [x0, x1) of the model's lgx
 };
 
+// Slice layout of a model (the slice kernel; a second copy of the CSC arrays of
+// Sec. 3.1 arranged for one lane per column). The owned states are cut into
+// windows of whole states of at most kSliceWindowCols columns; inside a window
+// the columns are ordered by length (longest first) and dealt to slices of 32
+// slots. Entry t of the column in slot l of a slice sits at off + 32 t + l, so a
+// warp reading entry t of its 32 columns reads one contiguous run; entries keep
+// their order within the column (a threshold hint names the same entry in both
+// layouts). A slice runs to its longest column (the lanes of shorter ones idle
+// without loads); ordering by length keeps that padding to a few percent.
+constexpr int kSliceWindowCols = 256;
+struct SliceMeta {
+  long long off;  // first entry of the slice in rows / lg
+  int32_t len;    // entries of its longest column (trips of the slice's loop)
+  int32_t pad;
+};
+struct SliceLayout {
+  int32_t n_windows = 0;
+  int32_t n_slices = 0;
+  int64_t entries = 0;              // entries including padding (32 per trip of every slice)
+  std::vector<int32_t> h_win_s0;    // n_windows + 1: state boundaries of the windows
+  std::vector<int32_t> h_win_sl0;   // n_windows + 1: slice boundaries of the windows
+  int2* slot = nullptr;             // 32 per slice: {column, entries in the slice arrays}; column -1: empty
+                                    // slot; 32-bit correction columns hold 0 entries here (their exact
+                                    // bounds are read from lgx)
+  SliceMeta* meta = nullptr;        // per slice
+  int32_t* rows = nullptr;          // destinations, padding 0
+  void* lg = nullptr;               // ulonglong2 (64-bit) or uint2 (32-bit) bound pairs, padding {0, 0}
+  void* block = nullptr;            // the one allocation holding the arrays above
+  size_t bytes = 0;
+};
+
 // Device-resident model (the "IntervalMDP.cu(problem)" transfer of Sec. 3.2,
 // CSC layout of Sec. 3.1 / Appendix A).
 struct DevModel {
@@ -86,6 +118,8 @@ struct DevModel {
   std::vector<int32_t> h_wide;      // wide states (in no tile)
   int2* wide = nullptr;             // device copy as (problem 0, state)
   int32_t n_wide = 0;
+  SliceLayout* slices = nullptr;    // built on first use by a session that runs the slice kernel
+  std::mutex slices_mu;
 };
 
 
@@ -106,6 +140,13 @@ struct alignas(16) Problem {
   int32_t* policy;        // nullable; see policy_mode
   const int64_t* rbias;   // reward: per-state term c_s of W_k = c_s + gamma T(W_{k-1}), signed Q2.62
   int32_t* hint;          // per column: entry that held the O-maximization threshold last iteration (-1: none)
+  // slice kernel only (nullptr otherwise): the model's slice layout and the
+  // per-column q of the running iteration
+  const int2* sl_slot;
+  const SliceMeta* sl_meta;
+  const int32_t* sl_rows;
+  const void* sl_lg;
+  uint64_t* qcol;
   int32_t n_states;
   int32_t pessimistic;
   int32_t maximize;
@@ -137,15 +178,17 @@ struct StepControl {
 
 // Launch configuration of the Bellman step (per session; chosen by rule or by
 // the autotuner). Zero fields mean "by rule".
-enum : int32_t { kKernelRule = 0, kKernelRing = 1, kKernelDirect = 2, kKernelTiny = 3 };
+enum : int32_t { kKernelRule = 0, kKernelRing = 1, kKernelDirect = 2, kKernelTiny = 3, kKernelSlice = 4 };
 // A session of one problem this small runs all its iterations in one launch of
 // one CTA, with the model and values in shared memory (bellman_tiny_kernel).
 constexpr int32_t kTinyMaxStates = 1024, kTinyMaxCols = 1024, kTinyMaxEntries = 4096;
 constexpr int kDirectWarps = 8;  // warps per CTA of the direct kernel
+constexpr int kSliceWarps = 8;   // warps per CTA of the slice kernel
 struct LaunchConfig {
-  int32_t kernel = kKernelRule;  // ring: TMA-fed shared-memory tiles; direct: warps stream tiles from global memory
-  int32_t cta_warps = 0;         // ring: 16 or 24 warps per CTA; direct: 8
-  int32_t ctas_per_sm = 0;       // direct: 3 or 4 CTAs per SM
+  int32_t kernel = kKernelRule;  // ring: TMA-fed shared-memory tiles; direct: warps stream tiles from global
+                                 // memory; slice: one lane per column over the slice layout
+  int32_t cta_warps = 0;         // ring: 16 or 24 warps per CTA; direct and slice: 8
+  int32_t ctas_per_sm = 0;       // direct and slice: 3 or 4 CTAs per SM
   int32_t tile_entries = 0;      // tile plan: entries per tile (<= kTileEntries)
   int32_t wide_col = 0;          // columns this long make their state wide
 };
@@ -189,6 +232,13 @@ struct StepLaunch {
   const int32_t* rank_tile_end;  // count: tiles of ranks 0..r
   int32_t tiny_ok;     // one small problem (sizes below): the single-CTA kernel may run it
   int32_t tiny_states, tiny_cols, tiny_entries;
+  // slice kernel: the work items (tile = window, slice of the model's layout) in
+  // tile order, the items of tiles [0, t] (per tile), and per tile the count of
+  // its slices finished in the running launch (zero between launches)
+  const int2* items;
+  const int32_t* tile_item_end;
+  unsigned int* win_cnt;
+  int32_t n_items;
   int32_t grid_total;  // CTAs of both step kernels in this launch (set by the launcher)
   int32_t stall;       // test hook: the producer issues nothing, so every wait runs out
 };
@@ -226,6 +276,12 @@ LaunchConfig resolve_launch(const StepLaunch& L, const LaunchConfig* cfg);
 // `fixed` entry (nullable; n_states of the problem) belong to neither.
 void plan_tiles(const DevModel* m, int32_t problem, std::vector<Tile>& out, std::vector<int32_t>& wide,
                 int32_t tile_entries = 0, int32_t wide_col = 0, const uint8_t* fixed = nullptr);
+
+// slices.cu
+// The model's slice layout, built on `st` on first use (thread-safe; kept until
+// the model is destroyed).
+imdp_status model_slice_layout(DevModel* m, cudaStream_t st, const SliceLayout** out);
+void slice_layout_free(SliceLayout* l);
 
 // model.cu
 // Per-iteration error budget of 32-bit storage when the caller names none:
@@ -274,6 +330,15 @@ struct Session {
   int2* wide = nullptr;
   int32_t n_wide = 0;
   int64_t wide_entries = 0;  // transitions of the wide states (host count)
+  // slice kernel: per-column q of every problem (offsets as `hints`), the work
+  // items and window counters of the installed plan
+  uint64_t* qbuf = nullptr;
+  int2* items = nullptr;
+  int32_t* tile_item_end = nullptr;
+  unsigned int* win_cnt = nullptr;
+  // Point every problem at its model's slice layout (built if needed) and
+  // allocate the per-column q; idempotent.
+  imdp_status prepare_slices(cudaStream_t st);
   SideStream side;  // created when the session has both tiles and wide states
   LaunchConfig cfg;  // launch configuration (rule, set_launch or the autotuner)
   StepLaunch L{};
@@ -291,7 +356,9 @@ struct Session {
   imdp_status reset(cudaStream_t st);
   // Upload a tile plan (tiles and wide states of every problem) and point the
   // launch at it.
-  imdp_status install_plan(const std::vector<Tile>& tiles, const std::vector<int2>& wide, cudaStream_t st);
+  // `slice`: the plan is the slice kernel's (windows), which also takes work items.
+  imdp_status install_plan(const std::vector<Tile>& tiles, const std::vector<int2>& wide, cudaStream_t st,
+                           bool slice = false);
   // Tile plan of every problem (rank order) under the plan limits of `c`,
   // leaving out the states the properties fix.
   void build_plan(const LaunchConfig& c, std::vector<Tile>& tiles, std::vector<int2>& wide) const;

@@ -206,6 +206,7 @@ void model_destroy(DevModel* m) {
                   (void*)m->tiles, (void*)m->wide, (void*)m->lg32, (void*)m->shift, (void*)m->xoff, (void*)m->lgx})
     if (p) cudaFreeAsync(p, nullptr);
   cudaStreamSynchronize(nullptr);
+  slice_layout_free(m->slices);
   delete m;
 }
 

@@ -8,7 +8,7 @@
 // keeps them in one file-scope device array instead.
 //
 // The array below is the only scratch. Every GPU that loads this library holds
-// it (kNoAllocBytes, about 2.7 MB) until the process exits. Its host-side name is
+// it (kNoAllocBytes, about 3.7 MB) until the process exits. Its host-side name is
 // only a stand-in: host code obtains the device address with
 // cudaGetSymbolAddress, once per device, on the first call made with that
 // device current (so that first call should happen before any stream capture).
@@ -36,9 +36,13 @@ constexpr size_t kOffFlag = 1024;
 constexpr size_t kOffMask = 1280;
 constexpr size_t kOffIdx = kOffMask + kNoAllocMaxStates;                 // reach + avoid indices
 constexpr size_t kOffV = kOffIdx + sizeof(int32_t) * kNoAllocMaxStates;  // 2 x n values
-constexpr size_t kNoAllocBytes = kOffV + 2 * sizeof(uint64_t) * kNoAllocMaxStates;
+// Per-column threshold hints (the warm start of the next iteration) for models
+// of up to kNoAllocMaxHintCols columns, padded as a session pads them.
+constexpr int32_t kNoAllocMaxHintCols = 262144;
+constexpr size_t kOffHint = kOffV + 2 * sizeof(uint64_t) * kNoAllocMaxStates;
+constexpr size_t kNoAllocBytes = kOffHint + sizeof(int32_t) * (((size_t)kNoAllocMaxHintCols + 3) / 4 * 4 + 4);
 static_assert(sizeof(Problem) <= 256 && sizeof(IterState) <= 256 && sizeof(StepControl) <= 256, "layout");
-static_assert(kOffIdx % 256 == 0 && kOffV % 256 == 0, "alignment");
+static_assert(kOffIdx % 256 == 0 && kOffV % 256 == 0 && kOffHint % 256 == 0, "alignment");
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -135,6 +139,7 @@ extern "C" IMDP_API imdp_status imdp_value_iteration_noalloc(imdp_model* m, cons
   uint8_t* d_mask = base + kOffMask;
   int32_t* d_idx = (int32_t*)(base + kOffIdx);
   uint64_t* d_V = (uint64_t*)(base + kOffV);
+  int32_t* d_hint = (int32_t*)(base + kOffHint);
   const int32_t n = dm->n_states;
 
   Problem P;
@@ -149,6 +154,10 @@ extern "C" IMDP_API imdp_status imdp_value_iteration_noalloc(imdp_model* m, cons
   P.xoff = dm->xoff;
   P.lgx = dm->lgx;
   P.fixed = d_mask;
+  // hints when the model's columns fit the fixed region (else every column
+  // takes the full threshold search, with the same result)
+  const bool hints = dm->n_cols <= kNoAllocMaxHintCols;
+  P.hint = hints ? d_hint : nullptr;
   P.V[0] = d_V;
   P.V[1] = d_V + n;
   P.n_states = n;
@@ -168,6 +177,8 @@ extern "C" IMDP_API imdp_status imdp_value_iteration_noalloc(imdp_model* m, cons
   // Re-initialise everything this call reads from the shared array.
   e = cudaMemsetAsync(base, 0, kOffMask, st);  // problem, iteration state, ticket, flag
   if (e == cudaSuccess) e = cudaMemsetAsync(d_mask, 0, n, st);
+  if (e == cudaSuccess && hints)  // -1: no hint yet (the previous call's hints belong to another query)
+    e = cudaMemsetAsync(d_hint, 0xff, sizeof(int32_t) * padded_i32((size_t)dm->n_cols), st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_prob, &P, sizeof(P), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_base, base_h, sizeof(base_h), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && spec->n_reach > 0)

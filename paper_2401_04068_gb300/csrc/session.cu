@@ -284,7 +284,8 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
   return IMDP_OK;
 }
 
-imdp_status Session::install_plan(const std::vector<Tile>& tl, const std::vector<int2>& wl, cudaStream_t st) {
+imdp_status Session::install_plan(const std::vector<Tile>& tl, const std::vector<int2>& wl, cudaStream_t st,
+                                  bool slice) {
   auto release = [&](void* p) {
     if (!p) return;
     allocs.erase(std::remove(allocs.begin(), allocs.end(), p), allocs.end());
@@ -294,9 +295,38 @@ imdp_status Session::install_plan(const std::vector<Tile>& tl, const std::vector
   if (e != cudaSuccess) return cuda_status(e, "session plan");
   release(tiles);
   release(wide);
+  release(items);
+  release(tile_item_end);
+  release(win_cnt);
+  items = nullptr;
+  tile_item_end = nullptr;
+  win_cnt = nullptr;
   tiles = alloc<Tile>(tl.size());
   wide = alloc<int2>(wl.size());
   if (!tiles || !wide) { set_error("device allocation failed (tile plan)"); return IMDP_ENOMEM; }
+  // slice kernel: one work item per slice of every window (tile), in tile order
+  std::vector<int2> it;
+  std::vector<int32_t> tend;
+  if (slice) {
+    tend.resize(tl.size());
+    for (size_t t = 0; t < tl.size(); ++t) {
+      for (int32_t g = tl[t].x0; g < tl[t].x1; ++g) it.push_back(make_int2((int32_t)t, g));
+      tend[t] = (int32_t)it.size();
+    }
+    items = alloc<int2>(it.size());
+    tile_item_end = alloc<int32_t>(tend.size());
+    win_cnt = alloc<unsigned int>(tl.size());
+    if (!items || !tile_item_end || !win_cnt) { set_error("device allocation failed (slice plan)"); return IMDP_ENOMEM; }
+    if (!it.empty()) e = cudaMemcpyAsync(items, it.data(), sizeof(int2) * it.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !tend.empty())
+      e = cudaMemcpyAsync(tile_item_end, tend.data(), sizeof(int32_t) * tend.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(win_cnt, 0, sizeof(unsigned int) * std::max<size_t>(tl.size(), 1), st);
+    if (e != cudaSuccess) return cuda_status(e, "session plan");
+  }
+  L.items = items;
+  L.tile_item_end = tile_item_end;
+  L.win_cnt = win_cnt;
+  L.n_items = (int32_t)it.size();
   if (!tl.empty()) e = cudaMemcpyAsync(tiles, tl.data(), sizeof(Tile) * tl.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !wl.empty())
     e = cudaMemcpyAsync(wide, wl.data(), sizeof(int2) * wl.size(), cudaMemcpyHostToDevice, st);
@@ -336,8 +366,59 @@ imdp_status Session::install_plan(const std::vector<Tile>& tl, const std::vector
   return IMDP_OK;
 }
 
+imdp_status Session::prepare_slices(cudaStream_t st) {
+  if (qbuf) return IMDP_OK;
+  for (int p = 0; p < count; ++p) {
+    const SliceLayout* l = nullptr;
+    imdp_status r = model_slice_layout(models[p], st, &l);
+    if (r != IMDP_OK) return r;
+  }
+  uint64_t* q = alloc<uint64_t>((size_t)total_cols);
+  if (!q) { set_error("device allocation failed (slice kernel)"); return IMDP_ENOMEM; }
+  cudaError_t e = cudaStreamSynchronize(st);  // launches in flight read the problem descriptors
+  if (e != cudaSuccess) return cuda_status(e, "slice kernel setup");
+  int64_t col_off = 0;
+  for (int p = 0; p < count; ++p) {
+    const SliceLayout* l = models[p]->slices;
+    Problem& P = probs_h[p];
+    P.sl_slot = l->slot;
+    P.sl_meta = l->meta;
+    P.sl_rows = l->rows;
+    P.sl_lg = l->lg;
+    P.qcol = q + col_off;  // same offsets as the hints
+    col_off += (int64_t)padded_i32(models[p]->n_cols);
+  }
+  e = cudaMemcpyAsync(probs, probs_h.data(), sizeof(Problem) * count, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "slice kernel setup");
+  qbuf = q;
+  return IMDP_OK;
+}
+
 void Session::build_plan(const LaunchConfig& c, std::vector<Tile>& tl, std::vector<int2>& wl) const {
   const LaunchConfig r = resolve_launch(L, &c);
+  if (r.kernel == kKernelSlice) {
+    // the windows of every problem's slice layout (prepare_slices built them);
+    // x0 / x1 are the window's slices
+    for (int p : order) {
+      const DevModel* m = models[p];
+      const SliceLayout* l = m->slices;
+      for (int32_t w = 0; w < l->n_windows; ++w) {
+        Tile T;
+        T.p = p;
+        T.s0 = l->h_win_s0[w];
+        T.s1 = l->h_win_s0[w + 1];
+        T.c0 = m->h_stateptr[T.s0];
+        T.c1 = m->h_stateptr[T.s1];
+        T.e0 = m->h_colptr[T.c0];
+        T.e1 = m->h_colptr[T.c1];
+        T.x0 = l->h_win_sl0[w];
+        T.x1 = l->h_win_sl0[w + 1];
+        tl.push_back(T);
+      }
+    }
+    return;
+  }
   for (int p : order) {
     std::vector<int32_t> ws;
     const size_t at = tl.size();
@@ -349,11 +430,16 @@ void Session::build_plan(const LaunchConfig& c, std::vector<Tile>& tl, std::vect
 
 imdp_status Session::set_launch(const LaunchConfig& c, cudaStream_t st) {
   const LaunchConfig old = resolve_launch(L, &cfg), now = resolve_launch(L, &c);
-  if (now.tile_entries != old.tile_entries || now.wide_col != old.wide_col) {
+  const bool slice = now.kernel == kKernelSlice;
+  if (now.tile_entries != old.tile_entries || now.wide_col != old.wide_col || slice != (old.kernel == kKernelSlice)) {
+    if (slice) {
+      imdp_status r = prepare_slices(st);
+      if (r != IMDP_OK) return r;
+    }
     std::vector<Tile> tl;
     std::vector<int2> wl;
     build_plan(c, tl, wl);
-    imdp_status r = install_plan(tl, wl, st);
+    imdp_status r = install_plan(tl, wl, st, slice);
     if (r != IMDP_OK) return r;
   }
   cfg = c;

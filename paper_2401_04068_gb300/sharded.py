@@ -64,10 +64,12 @@ class SliceRunner:
 
     ``m``: the whole model's host CSC arrays (n_states, stateptr, colptr, rowval,
     lower, upper); ``bounds``: the partition; ``spec_kw``: the specification
-    (``make_spec`` keywords, identical on every rank)."""
+    (``make_spec`` keywords, identical on every rank); ``launch``: launch
+    configuration keywords of the slice's session (``imdp_session_set_launch``;
+    None: by rule)."""
 
     def __init__(self, m, bounds: Sequence[int], part: int, spec_kw: dict, dtype=B.IMDP_F64, stream=None,
-                 device=None):
+                 device=None, launch: Optional[dict] = None):
         import torch
         self.bounds = [int(b) for b in bounds]
         self.part = part
@@ -79,6 +81,8 @@ class SliceRunner:
         self.model = B.create_model_slice(m, self.s0, self.s1, dtype, stream)
         self.spec = B.make_spec(**spec_kw)
         self.session = B.imdp_session_create([self.model], [self.spec], stream=stream)
+        if launch:
+            B.imdp_session_set_launch(self.session, stream=stream, **launch)
         self.eps_raw = B.imdp_session_stop_threshold(self.session, 0) if self.infinite else None
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.own = torch.empty(self.s1 - self.s0, dtype=torch.int64, device=dev)

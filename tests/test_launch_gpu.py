@@ -1,9 +1,11 @@
 """Launch configurations of the Bellman step and the autotuner, through the C ABI.
 
-Every configuration (ring or direct kernel, warps per CTA, CTAs per SM, tile
-size, wide-state threshold) must compute the same words: each column's value
-is the same multiset of exact integer terms whichever kernel runs it. Checked
-bitwise between configurations and against the oracle within TOL_F64."""
+Every configuration (ring, direct or slice kernel, warps per CTA, CTAs per SM,
+tile size, wide-state threshold) must compute the same words: each column's
+value is the same multiset of exact integer terms whichever kernel runs it,
+and every kernel takes the same path (warm start, neighbour check or search)
+for a column given the same hint. Checked bitwise between configurations and
+against the oracle within TOL_F64."""
 import json
 import os
 
@@ -25,6 +27,8 @@ CONFIGS = [
     dict(kernel=g.KERNEL_RING, cta_warps=16, tile_entries=700, wide_col=200),
     dict(kernel=g.KERNEL_DIRECT, ctas_per_sm=4, wide_col=1 << 30),
     dict(kernel=g.KERNEL_DIRECT, ctas_per_sm=3, wide_col=150),
+    dict(kernel=g.KERNEL_SLICE, ctas_per_sm=4),
+    dict(kernel=g.KERNEL_SLICE, ctas_per_sm=3),
 ]
 
 
@@ -95,14 +99,16 @@ def test_heterogeneous_batch_direct_equals_ring():
     models = [g.create_model(x) for x in ms]
     specs = [g.make_spec(horizon=10 + 5 * i, reach=x.goal, pessimistic=i % 2 == 0) for i, x in enumerate(ms)]
     outs = {}
-    for cfg in (dict(kernel=g.KERNEL_RING), dict(kernel=g.KERNEL_DIRECT, ctas_per_sm=4, tile_entries=256)):
+    for cfg in (dict(kernel=g.KERNEL_RING), dict(kernel=g.KERNEL_DIRECT, ctas_per_sm=4, tile_entries=256),
+                dict(kernel=g.KERNEL_SLICE)):
         sess = g.imdp_session_create(models, specs)
         g.imdp_session_set_launch(sess, **cfg)
         g.imdp_session_run(sess)
         outs[cfg["kernel"]] = [g.imdp_session_checkpoint(sess, i) for i in range(len(ms))]
         sess.close()
-    for (ra, ka), (rb, kb) in zip(outs[g.KERNEL_RING], outs[g.KERNEL_DIRECT]):
-        assert ka == kb and np.array_equal(ra, rb)
+    for other in (g.KERNEL_DIRECT, g.KERNEL_SLICE):
+        for (ra, ka), (rb, kb) in zip(outs[g.KERNEL_RING], outs[other]):
+            assert ka == kb and np.array_equal(ra, rb)
 
 
 def test_autotune_picks_a_config_and_caches_it(tmp_path):
@@ -112,7 +118,7 @@ def test_autotune_picks_a_config_and_caches_it(tmp_path):
     cache = str(tmp_path / "tuned.json")
     sess = g.imdp_session_create([model], [spec])
     cfg, ms = g.imdp_session_autotune(sess, 8, cache)
-    assert ms > 0 and cfg["kernel"] in (g.KERNEL_RING, g.KERNEL_DIRECT)
+    assert ms > 0 and cfg["kernel"] in (g.KERNEL_RING, g.KERNEL_DIRECT, g.KERNEL_SLICE)
     data = json.load(open(cache))
     assert len(data) == 1
     entry = next(iter(data.values()))
@@ -132,7 +138,8 @@ def test_autotune_picks_a_config_and_caches_it(tmp_path):
     assert os.path.exists(cache)
 
 
-@pytest.mark.parametrize("cfg", [dict(kernel=g.KERNEL_RING), dict(kernel=g.KERNEL_DIRECT, tile_entries=512)])
+@pytest.mark.parametrize("cfg", [dict(kernel=g.KERNEL_RING), dict(kernel=g.KERNEL_DIRECT, tile_entries=512),
+                                 dict(kernel=g.KERNEL_SLICE)])
 def test_finished_problems_leave_the_tile_walk(cfg):
     # Problems of different horizons (the longest not first) and one infinite
     # horizon in one session: launches walk only the running problems' tiles.
@@ -250,3 +257,65 @@ def test_single_cta_kernel_stepwise_and_restore():
     np.testing.assert_allclose(rc.astype(np.float64), ra.astype(np.float64), rtol=0, atol=1e-13 * 2.0 ** 63)
     for s_ in (a, b, c):
         s_.close()
+
+
+def _windows(stateptr, cap=256):
+    # windows of the slice layout: whole states, at most `cap` columns, one state at least
+    n, s, w = len(stateptr) - 1, 0, 0
+    while s < n:
+        cols = 0
+        while s < n and (cols == 0 or cols + stateptr[s + 1] - stateptr[s] <= cap):
+            cols += stateptr[s + 1] - stateptr[s]
+            s += 1
+        w += 1
+    return w
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_slice_kernel_windows_switching_and_policy(dtype):
+    # States of up to 600 actions (a state of more than 256 columns is a window
+    # of its own, several slices, columns dealt by length) beside a model of
+    # single-action states; the kernel switched between steps (hints and values
+    # carry over); time-dependent policies and the slice layout's windows, all
+    # equal to the ring kernel's, to the bit.
+    ms = [random_imdp(30, max_actions=600, density=0.3, seed=72),
+          banded_imdp(700, 1, 700 * 90 + 700 + 1, eps=0.1, seed=73)]
+    budget = 1.5e-9 if dtype == "f32" else None
+    models = [g.create_model(x, dtype=g.IMDP_F32 if dtype == "f32" else g.IMDP_F64, budget=budget) for x in ms]
+    K = 24
+    specs = [g.make_spec(horizon=K, reach=x.goal, pessimistic=i == 0) for i, x in enumerate(ms)]
+    pol_ref = None
+    runs = [[(K, dict(kernel=g.KERNEL_RING))],
+            [(K, dict(kernel=g.KERNEL_SLICE))],
+            [(5, dict(kernel=g.KERNEL_SLICE)), (6, dict(kernel=g.KERNEL_DIRECT, tile_entries=700)),
+             (7, dict(kernel=g.KERNEL_SLICE, ctas_per_sm=3)), (6, dict(kernel=g.KERNEL_RING))]]
+    ref = None
+    for plan in runs:
+        sess = g.imdp_session_create(models, specs, want_policy=[1, 1])
+        for n, cfg in plan:
+            g.imdp_session_set_launch(sess, **cfg)
+            g.imdp_session_step(sess, n)
+        words = [g.imdp_session_checkpoint(sess, i) for i in range(2)]
+        pols = []
+        for i, x in enumerate(ms):
+            pol = np.zeros((K, x.n_states), np.int32)
+            g.imdp_session_read(sess, i, None, None, None, pol)
+            pols.append(pol)
+        if plan[0][1]["kernel"] == g.KERNEL_SLICE and len(plan) == 1:
+            nt, nw, _ = g.imdp_session_plan(sess)
+            assert nw == 0 and nt == sum(_windows(x.stateptr) for x in ms)
+        sess.close()
+        if ref is None:
+            ref = (words, pols)
+            for i, x in enumerate(ms):
+                _, oV, _, _, _ = run_oracle(x, horizon=K, reach=x.goal, pessimistic=i == 0)
+                V = words[i][0].astype(np.float64) / 2.0 ** 63
+                tol = K * models[i].error_bound() + TOL_F64 if dtype == "f32" else TOL_F64
+                assert float(np.max(np.abs(V - oV))) <= tol
+        else:
+            for (ra, ka), (rb, kb) in zip(ref[0], words):
+                assert ka == kb == K and np.array_equal(ra, rb)
+            for pa, pb in zip(ref[1], pols):
+                assert np.array_equal(pa, pb)
+    for x in models:
+        x.close()

@@ -15,9 +15,9 @@ from workloads import banded_imdp, random_imdp
 pytestmark = pytest.mark.gpu
 
 
-def _lockstep(m, parts, spec_kw, dtype=g.IMDP_F64):
+def _lockstep(m, parts, spec_kw, dtype=g.IMDP_F64, launch=None):
     b = g.imdp_partition_states(m.n_states, m.stateptr, m.colptr, parts)
-    runners = [SliceRunner(m, b, r, spec_kw, dtype) for r in range(parts)]
+    runners = [SliceRunner(m, b, r, spec_kw, dtype, launch=launch) for r in range(parts)]
     for r in runners:
         r.reset()
     for _ in range(runners[0].horizon):
@@ -49,11 +49,13 @@ def _whole(m, spec_kw, dtype=g.IMDP_F64):
 
 @pytest.mark.parametrize("parts", [2, 3])
 @pytest.mark.parametrize("pess,maxi", [(True, True), (False, False)])
-def test_sharded_equals_whole_reach(parts, pess, maxi):
+@pytest.mark.parametrize("kernel", [g.KERNEL_RULE, g.KERNEL_SLICE])
+def test_sharded_equals_whole_reach(parts, pess, maxi, kernel):
+    # the slice kernel lays out the owned states of each slice only
     m = banded_imdp(600, 2, 600 * 2 * 25 + 1, seed=81)
     kw = dict(horizon=40, reach=m.goal, pessimistic=pess, maximize=maxi)
     Vw, kw_ = _whole(m, kw)
-    b, outs = _lockstep(m, parts, kw)
+    b, outs = _lockstep(m, parts, kw, launch=dict(kernel=kernel) if kernel else None)
     for V, k in outs:
         assert k == kw_ == 40
         np.testing.assert_array_equal(V, Vw)  # every slice holds the whole iterate after the last exchange

@@ -1,4 +1,4 @@
-"""Failure detection on the GPU without a fault: with the test hook set, the tiled
+"""Failure detection on the GPU without a fault: with the test hook set, the ring
 kernel's producer issues no copies, so every consumer wait runs into its bound
 (about 2 s). The kernel records the error and returns; the host reads
 IMDP_ETIMEOUT; the context stays usable and the next run is correct."""
@@ -18,6 +18,9 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     m = banded_imdp(200, 1, 200 * 10 + 1, seed=95)
     model = g.create_model(m)
     sess = g.imdp_session_create([model], [g.make_spec(horizon=3, reach=m.goal)])
+    # the hook starves the ring kernel's waits; a model this small would
+    # otherwise run on the single-CTA kernel, which has none
+    g.imdp_session_set_launch(sess, kernel=g.KERNEL_RING)
     V = np.zeros(m.n_states)
     g.imdp_debug_stall_producer(True)
     try:

@@ -77,10 +77,9 @@ def test_noalloc_with_wide_states_matches_regular():
         g.imdp_value_iteration(model, spec, ref)
         out = torch.zeros(m.n_states, dtype=torch.float64, device="cuda")
         assert g.imdp_value_iteration_noalloc(model, spec, out) == g.IMDP_OK
-        # the entry point keeps no per-column threshold hints, so every column
-        # takes the full search, whose products are truncated in another grouping
-        # than the warm start's: equal up to K * k_max * 2^-62 (~2e-14 here)
-        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=1e-13)
+        # the entry point keeps threshold hints in its fixed array (the model's
+        # columns fit), so it iterates exactly as the session path does
+        np.testing.assert_array_equal(out.cpu().numpy(), ref)
 
 
 def test_noalloc_against_the_oracle_directly():
@@ -119,3 +118,19 @@ def test_noalloc_32bit_storage_model():
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
     _, oV, _, _, _ = run_oracle(m, horizon=K, reach=m.goal)
     assert float(np.max(np.abs(got - oV))) <= K * model.error_bound() + TOL_F64
+
+
+def test_noalloc_without_room_for_hints():
+    # more columns than the fixed array's hint region holds (262,144): every
+    # column takes the full threshold search each iteration; the answer equals
+    # the session path's up to the 64-bit products' truncation
+    import torch
+    m = banded_imdp(100000, 3, 100000 * 3 * 4 + 100000 * 3 + 1, eps=0.1, seed=37)
+    assert m.n_cols > 262144
+    model = g.create_model(m)
+    spec = g.make_spec(horizon=12, reach=m.goal)
+    ref = np.zeros(m.n_states)
+    g.imdp_value_iteration(model, spec, ref)
+    out = torch.zeros(m.n_states, dtype=torch.float64, device="cuda")
+    assert g.imdp_value_iteration_noalloc(model, spec, out) == g.IMDP_OK
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=1e-13)
