@@ -267,7 +267,9 @@ def run_ours(args, rank, world, local_rank):
     else:
         spec = g.make_spec(horizon=args.horizon, reach=m.goal, pessimistic=True, maximize=True)
     sess = g.imdp_session_create([model], [spec], want_policy=[1] if args.policy else None, stream=stream)
-    launch = apply_launch(g, sess, args, stream, min(args.horizon, 64) if not args.infinite else 64)
+    # tuned on the query's own iterations: early iterations (many threshold
+    # searches) and late ones (warm starts) favour different kernels
+    launch = apply_launch(g, sess, args, stream, min(args.horizon, 200) if not args.infinite else 64)
 
     def one_step(ev=None):
         g.imdp_session_reset(sess, stream)
