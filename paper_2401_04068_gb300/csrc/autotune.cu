@@ -253,6 +253,7 @@ IMDP_API imdp_status imdp_session_autotune(imdp_session* s, int32_t iters, const
     add(kKernelDirect, kDirectWarps, 4, kTileEntries, kWideCol);
     add(kKernelDirect, kDirectWarps, 3, kTileEntries, kWideCol);
     add(kKernelDirect, kDirectWarps, 4, 1024, kWideCol);
+    add(kKernelDirect, kDirectWarps, 3, 1024, kWideCol);
     add(kKernelSlice, kSliceWarps, 4, kTileEntries, kWideCol);
     add(kKernelSlice, kSliceWarps, 3, kTileEntries, kWideCol);
     bool have = false;

@@ -361,8 +361,17 @@ struct RowsOf<2> {
   typedef SRows type;
 };
 
+// Entry idx's destination when `ok`, else 0 (a valid state); from global
+// memory a predicated load, which the compiler may schedule freely.
+__device__ __forceinline__ int32_t row_if(const int32_t* rows, int idx, bool ok) { return ok ? rows[idx] : 0; }
+__device__ __forceinline__ int32_t row_if(GRows rows, int idx, bool ok) { return ld_stream_i32_if(rows.p + idx, ok); }
+__device__ __forceinline__ int32_t row_if(SRows rows, int idx, bool ok) {
+  return ld_stream_i32_if(rows.p + (size_t)idx * kSliceStride, ok);
+}
+
 // Bounds of one column as {lower, gap} in Q1.63, from 64-bit storage or from
 // 32-bit mantissas shifted up by `down` = 32 - shift_j; read as `gmem` says.
+// `at_if`: entry idx's pair when `ok`, else {0, 0} (predicated in global memory).
 template <bool f32, int gmem = 0>
 struct Bounds {
   const void* p;
@@ -374,6 +383,15 @@ struct Bounds {
       return make_ulonglong2((uint64_t)m.x << down, (uint64_t)m.y << down);
     }
     return gmem ? ld_stream_u64x2(static_cast<const ulonglong2*>(p) + at) : static_cast<const ulonglong2*>(p)[at];
+  }
+  __device__ __forceinline__ ulonglong2 at_if(int idx, bool ok) const {
+    if (gmem == 0) return ok ? (*this)[idx] : make_ulonglong2(0, 0);
+    const size_t at = gmem == 2 ? (size_t)idx * kSliceStride : (size_t)idx;
+    if (f32) {
+      const uint2 m = ld_stream_u32x2_if(static_cast<const uint2*>(p) + at, ok);
+      return make_ulonglong2((uint64_t)m.x << down, (uint64_t)m.y << down);
+    }
+    return ld_stream_u64x2_if(static_cast<const ulonglong2*>(p) + at, ok);
   }
 };
 
@@ -405,12 +423,31 @@ __device__ __forceinline__ void warm_pass(const typename RowsOf<gmem>::type rows
                                           uint64_t& acc, uint64_t& flt, uint64_t& geq) {
   uint32_t fc = 0, gc = 0;
   const int nb = (k + 31) >> 5;
+  // from global memory the loop is software-pipelined: the next trip's
+  // destination and bounds are requested before this trip's gather (from
+  // shared memory, where the loads are short, the plain loop is faster)
+  constexpr bool pipe = gmem != 0;
+  int idx = lane;
+  int32_t r = 0;
+  ulonglong2 b = make_ulonglong2(0, 0);
+  if (pipe) {
+    r = row_if(rows, idx, idx < k);
+    b = lg.at_if(idx, idx < k);
+  }
 #pragma unroll 2
   for (int it = 0; it < nb; ++it) {
-    const int idx = it * 32 + lane;
-    const bool ok = idx < k;
-    const uint64_t v = V.at(ok ? rows[idx] : 0);
-    const ulonglong2 b = ok ? lg[idx] : make_ulonglong2(0, 0);
+    if (!pipe) {
+      r = row_if(rows, idx, idx < k);
+      b = lg.at_if(idx, idx < k);
+    }
+    const uint64_t v = V.at(r);
+    idx += 32;
+    int32_t rn = 0;
+    ulonglong2 bn = make_ulonglong2(0, 0);
+    if (pipe) {
+      rn = row_if(rows, idx, idx < k);
+      bn = lg.at_if(idx, idx < k);
+    }
     const bool below = pess ? (v < vk) : (v > vk);
     acc += __umul64hi(v, b.x + (below ? b.y : 0ull));
     const uint64_t gb = below ? b.y : 0ull, ge = v == vk ? b.y : 0ull;
@@ -419,6 +456,10 @@ __device__ __forceinline__ void warm_pass(const typename RowsOf<gmem>::type rows
     if (carry) {
       fc += flt < gb ? 1u : 0u;
       gc += geq < ge ? 1u : 0u;
+    }
+    if (pipe) {
+      r = rn;
+      b = bn;
     }
   }
   if (carry) {
@@ -442,18 +483,39 @@ __device__ __forceinline__ void warm_pass32(const typename RowsOf<gmem>::type ro
                                             int32_t k, const VP V, uint32_t vk, int s, bool pess,
                                             int lane, uint64_t& acc, uint64_t& flt, uint64_t& geq) {
   const int nb = (k + 31) >> 5;
+  if (gmem == 0) {
+#pragma unroll 4
+    for (int it = 0; it < nb; ++it) {
+      const int idx = it * 32 + lane;
+      const bool ok = idx < k;
+      const uint32_t v = V.hi(ok ? rows[idx] : 0);
+      uint2 b = make_uint2(0, 0);
+      if (ok) b = m[idx];
+      const bool below = pess ? (v < vk) : (v > vk);
+      const uint32_t g = below ? b.y : 0u;
+      acc += ((uint64_t)v * (uint64_t)(b.x + g)) >> s;
+      flt += g;
+      geq += v == vk ? b.y : 0u;
+    }
+    return;
+  }
+  // global memory: software-pipelined as in warm_pass
+  int idx = lane;
+  int32_t r = row_if(rows, idx, idx < k);
+  uint2 b = ld_stream_u32x2_if(m + idx, idx < k);
 #pragma unroll 4
   for (int it = 0; it < nb; ++it) {
-    const int idx = it * 32 + lane;
-    const bool ok = idx < k;
-    const uint32_t v = V.hi(ok ? rows[idx] : 0);
-    uint2 b = make_uint2(0, 0);
-    if (ok) b = gmem ? ld_stream_u32x2(m + idx) : m[idx];
+    const uint32_t v = V.hi(r);
+    idx += 32;
+    const int32_t rn = row_if(rows, idx, idx < k);
+    const uint2 bn = ld_stream_u32x2_if(m + idx, idx < k);
     const bool below = pess ? (v < vk) : (v > vk);
     const uint32_t g = below ? b.y : 0u;
     acc += ((uint64_t)v * (uint64_t)(b.x + g)) >> s;
     flt += g;
     geq += v == vk ? b.y : 0u;
+    r = rn;
+    b = bn;
   }
 }
 
