@@ -795,6 +795,8 @@ def run_state_sharded(args, rank, world, local_rank):
     bounds = g.imdp_partition_states(m.n_states, m.stateptr, m.colptr, world)
     lengths = np.diff(bounds)
     runner = SliceRunner(m, bounds, rank, dict(horizon=args.horizon, reach=m.goal), dtype)
+    # each slice's session takes the autotuner's configuration for its own shape
+    launch = apply_launch(g, runner.session, args, None, min(args.horizon, 200))
 
     def one_step():
         runner.reset()
@@ -830,7 +832,7 @@ def run_state_sharded(args, rank, world, local_rank):
     if rank != 0:
         return
     cfg = workload_config(args.workload, m, args.horizon)
-    cfg.update(parallelism=f"state-sharded x{world}", partition=[int(x) for x in bounds])
+    cfg.update(parallelism=f"state-sharded x{world}", partition=[int(x) for x in bounds], launch=launch)
     out = {
         "metric": METRIC, "value": units / (elapsed_ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,

@@ -109,10 +109,21 @@ class SliceRunner:
         """Write the other parts' V_k (``slices[r]`` for part r) into this slice."""
         for r, x in enumerate(slices):
             if r != self.part and x.numel():
+                if self.stream is not None:
+                    x.record_stream(self.stream)  # read there after the exchange's stream lets go of it
                 B.imdp_session_values_put(self.session, 0, self.k, self.bounds[r], self.bounds[r + 1], x,
                                           self.stream)
 
     def sync(self):
+        """Order the exchange after this step on the device: the exchange runs on
+        torch's current stream, which waits for the slice's stream (the host does
+        not block; a residual read on the host waits by itself)."""
+        if self.stream is not None:
+            import torch
+            torch.cuda.current_stream().wait_stream(self.stream)
+
+    def wait(self):
+        """Block the host until the slice's work is done."""
         if self.stream is not None:
             self.stream.synchronize()
 
@@ -134,7 +145,7 @@ def drive(runner, exchange: Callable, lengths: Sequence[int], rank: int) -> int:
     for _ in range(runner.horizon):
         own = runner.step()
         res = runner.residual() if runner.infinite else None
-        runner.sync()  # `own` and the residual are complete before the exchange reads them
+        runner.sync()  # the exchange reads `own` and the residual after the step writes them
         slices, rmax = exchange(own, res, lengths, rank)
         runner.put(slices)
         if runner.infinite and rmax < runner.eps_raw:
@@ -163,7 +174,7 @@ def run_sharded(m, spec_kw: dict, rank: int, world: int, group=None, dtype=B.IMD
         V = np.zeros(m.n_states)
         kk = [0]
         runner.read(V, kk)
-        runner.sync()
+        runner.wait()
         torch.cuda.synchronize()
         assert kk[0] == k
         return V, k

@@ -140,3 +140,30 @@ def test_slice_errors():
     with pytest.raises(g.ImdpError):
         g.imdp_create_csc_slice(m.n_states, 0, 49, len(cp) - 1, len(rv), sp, cp, rv, lo, up)
     sm.close()
+
+
+def test_run_sharded_through_nccl_on_a_side_stream():
+    # The library's driver as a caller runs it: one rank of an NCCL group, the
+    # slice's session on its own stream, the exchange ordered after each step
+    # on the device (no host wait per step); finite and infinite horizons equal
+    # the unsharded session word for word.
+    import socket
+    import torch.distributed as dist
+    from paper_2401_04068_gb300.sharded import run_sharded
+    if dist.is_initialized():
+        pytest.skip("a process group is already initialised")
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    try:
+        m = banded_imdp(700, 2, 700 * 2 * 30 + 1, seed=86)
+        st = torch.cuda.Stream()
+        for kw in (dict(horizon=60, reach=m.goal),
+                   dict(infinite_time=True, eps=1e-8, horizon=100000, reach=m.goal)):
+            Vw, kw_ = _whole(m, kw)
+            V, k = run_sharded(m, kw, 0, 1, stream=st)
+            assert k == kw_
+            np.testing.assert_array_equal(V, Vw)
+    finally:
+        dist.destroy_process_group()
