@@ -462,6 +462,77 @@ def _gpu_setup(rank, world, local_rank):
     return torch.device("cuda", local_rank)
 
 
+def run_polished(args, rank, world, local_rank):
+    """Infinite horizon on 32-bit storage, polished on the 64-bit model
+    (imdp_value_iteration_polished): one step = one whole query from V_0 to the
+    64-bit stopping test; units = transitions x all iterations (both phases)."""
+    import torch
+    import paper_2401_04068_gb300 as g
+    dev = _gpu_setup(rank, world, local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    m = make_workload(args.workload, rank, args.models)
+    m32 = g.create_model(m, dtype=g.IMDP_F32, stream=stream, budget=f32_budget(args))
+    m64 = g.create_model(m, dtype=g.IMDP_F64, stream=stream)
+    spec = g.make_spec(infinite_time=True, eps=args.eps, horizon=1000000, reach=m.goal, pessimistic=True,
+                       maximize=True)
+    launches = []
+    for mdl in (m32, m64):  # the autotuner's configuration of each storage
+        s_ = g.imdp_session_create([mdl], [spec], stream=stream)
+        launches.append(apply_launch(g, s_, args, stream, 64))
+        s_.close()
+    Vd = torch.empty(m.n_states, dtype=torch.float64, device=dev)
+    res = torch.empty(m.n_states, dtype=torch.float64, device=dev)
+
+    def one_step():
+        k = [0]
+        st, k32 = g.imdp_value_iteration_polished(m32, m64, spec, Vd, k, res, stream=stream,
+                                                  launch32=launches[0], launch64=launches[1])
+        assert st == g.IMDP_OK
+        return k32, k[0]
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        iters.append(one_step())
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    my_units = float(m.nnz) * sum(k for _, k in iters)
+    elapsed_ms, _, total_units = reduce_across_ranks(elapsed_ms, 0.0, my_units, world, dev)
+    if rank != 0:
+        return
+    k32, k = iters[-1]
+    cfg = workload_config(args.workload, m, args.horizon)
+    cfg.update(horizon=f"infinite (eps {args.eps:g}); {k32} iterations on 32-bit storage, then {k - k32} "
+                       f"on 64-bit (stopping test of the 64-bit path)",
+               query="maximize pessimistic reachability, infinite horizon",
+               storage="32-bit + correction to its fixed point, polished with 64-bit sweeps",
+               launch={"f32": launches[0], "f64": launches[1]},
+               error_bound_per_iteration_f32=m32.error_bound())
+    out = {
+        "metric": METRIC.replace("finite reachability K=200", "infinite-horizon reachability (to convergence)"),
+        "value": total_units / (elapsed_ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32+u64",
+        "data": "synthetic (seeded banded IMDPs shaped like the paper's benchmark table)", "config": cfg,
+        "roofline": None, "clocks": clk, "e2e": None,
+        "note": "each step creates its two sessions (imdp_value_iteration_polished), inside the timed region",
+    }
+    print(json.dumps(out), flush=True)
+
+
 def run_uneven(args, rank, world, local_rank):
     """Heterogeneous batch: 10,000 problems of different shapes and horizons in one
     resident session; a step runs every problem to its own horizon."""
@@ -868,6 +939,8 @@ def main():
     ap.add_argument("--client-threads", type=int, default=4, help="served workload: frontend threads")
     ap.add_argument("--policy", action="store_true", help="also synthesize the time-dependent policy (K x n)")
     ap.add_argument("--infinite", action="store_true", help="infinite horizon: iterate until max |dV| < eps")
+    ap.add_argument("--polish", action="store_true",
+                    help="with --infinite: 32-bit storage to its fixed point, then 64-bit sweeps")
     ap.add_argument("--eps", type=float, default=1e-6, help="convergence tolerance of --infinite")
     ap.add_argument("--shard", default="problems", choices=["problems", "states"],
                     help="multi-GPU split: independent problems per rank (default) or one model's states")
@@ -891,6 +964,8 @@ def main():
             run_served(args, rank, world, local_rank)
         elif args.shard == "states":
             run_state_sharded(args, rank, world, local_rank)
+        elif args.polish:
+            run_polished(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

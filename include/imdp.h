@@ -212,6 +212,7 @@ IMDP_API void imdp_debug_stall_producer(int32_t on);
 IMDP_API imdp_status imdp_value_iteration(imdp_model* m, const imdp_spec* spec, double* V_out, int32_t* k_out,
                                  double* residual_out, int32_t* policy_out, void* stream);
 
+
 /*
  * Run `count` independent problems (models[i], specs[i]) together: every
  * Bellman iteration of every problem that is still running is one kernel
@@ -352,6 +353,29 @@ IMDP_API imdp_status imdp_session_plan(const imdp_session* s, int32_t* n_tiles, 
  */
 IMDP_API imdp_status imdp_session_autotune(imdp_session* s, int32_t iters, const char* cache_path, void* stream,
                                            imdp_launch_config* chosen, double* ms_per_iter);
+
+/*
+ * Infinite-horizon value iteration on 32-bit storage with 64-bit polishing (no
+ * counterpart in the paper, which computes in binary64 throughout; Sec. 3.2).
+ * The query `spec` (infinite_time required) first runs on m32 (IMDP_F32) until
+ * its residual test passes; the 64-bit model m64 (IMDP_F64, the same IMDP: equal
+ * structure, on the same device) then continues from that iterate, with the
+ * 32-bit run's threshold hints, until the 64-bit residual test passes (at least
+ * one 64-bit sweep). The result therefore meets the same stopping test as
+ * imdp_value_iteration on m64, after fewer 64-bit sweeps.
+ *   cfg32, cfg64 launch configurations of the two phases (nullable: by rule;
+ *                as imdp_session_set_launch)
+ *   V_out        double[n_states] (host or device), the polished values
+ *   k32_out      int32 (host, nullable): iterations on 32-bit storage
+ *   k_out        int32 (host, nullable): all iterations (32-bit + 64-bit)
+ *   residual_out, policy_out: as imdp_value_iteration, from the 64-bit phase
+ * IMDP_EINVAL for NULL arguments, wrong storage types, different structures,
+ * state slices or a finite horizon. Synchronizes `stream`.
+ */
+IMDP_API imdp_status imdp_value_iteration_polished(imdp_model* m32, imdp_model* m64, const imdp_spec* spec,
+                                                   const imdp_launch_config* cfg32, const imdp_launch_config* cfg64,
+                                                   double* V_out, int32_t* k32_out, int32_t* k_out,
+                                                   double* residual_out, int32_t* policy_out, void* stream);
 /*
  * State-sharded value iteration (one model split over several GPUs).
  * Sec. 4 notes that the per-state problems of Eq. 2 are independent within an

@@ -35,7 +35,7 @@ EXPORTED = [
     "imdp_session_checkpoint", "imdp_session_restore",
     "imdp_session_set_launch", "imdp_session_get_launch", "imdp_session_autotune", "imdp_session_plan",
     "imdp_create_csc_f32", "imdp_model_exact_columns", "imdp_session_residual", "imdp_session_stop_threshold",
-    "imdp_server_set_launch", "imdp_server_stats",
+    "imdp_server_set_launch", "imdp_server_stats", "imdp_value_iteration_polished",
 ]
 
 
@@ -126,6 +126,9 @@ def load(path: Optional[str] = None):
     lib.imdp_model_info.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_size_t), C.POINTER(C.c_int32)]
     lib.imdp_value_iteration.argtypes = [vp, C.POINTER(imdp_spec), vp, C.POINTER(C.c_int32), vp, vp, vp]
+    lib.imdp_value_iteration_polished.argtypes = [vp, vp, C.POINTER(imdp_spec), C.POINTER(imdp_launch_config),
+                                                  C.POINTER(imdp_launch_config), vp, C.POINTER(C.c_int32),
+                                                  C.POINTER(C.c_int32), vp, vp, vp]
     lib.imdp_value_iteration_batch.argtypes = [C.POINTER(vp), C.POINTER(imdp_spec), C.c_int32, C.POINTER(vp),
                                                C.POINTER(C.c_int32), vp]
     lib.imdp_session_create.argtypes = [C.POINTER(vp), C.POINTER(imdp_spec), C.c_int32, vp, vp, C.POINTER(vp)]
@@ -336,6 +339,31 @@ def imdp_value_iteration(model: Model, spec, V_out, k_out=None, residual_out=Non
     if check and st not in (IMDP_OK, IMDP_ENOCONV):
         _check(st, "imdp_value_iteration")
     return st
+
+
+def imdp_value_iteration_polished(model32: Model, model64: Model, spec, V_out, k_out=None, residual_out=None,
+                                  policy_out=None, stream=None, check=True, launch32: Optional[dict] = None,
+                                  launch64: Optional[dict] = None):
+    """Raw call: the infinite-horizon query on 32-bit storage, then polished on the
+    64-bit model (``launch32`` / ``launch64``: launch configuration fields of the
+    two phases, None: by rule). Returns (status, iterations on 32-bit storage); all
+    iterations go to ``k_out[0]`` when given."""
+    def cfg(d):
+        if d is None:
+            return None
+        c = imdp_launch_config()
+        for f, _ in imdp_launch_config._fields_:
+            setattr(c, f, int(d.get(f, 0)))
+        return C.byref(c)
+    k32, k = C.c_int32(0), C.c_int32(0)
+    st = load().imdp_value_iteration_polished(C.c_void_p(model32.handle), C.c_void_p(model64.handle), C.byref(spec),
+                                              cfg(launch32), cfg(launch64), _ptr(V_out), C.byref(k32), C.byref(k),
+                                              _ptr(residual_out), _ptr(policy_out), _stream(stream))
+    if k_out is not None:
+        k_out[0] = k.value
+    if check and st not in (IMDP_OK, IMDP_ENOCONV):
+        _check(st, "imdp_value_iteration_polished")
+    return st, k32.value
 
 
 def imdp_value_iteration_batch(models: Sequence[Model], specs: Sequence, V_out: Sequence, k_out=None, stream=None,

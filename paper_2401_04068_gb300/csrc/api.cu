@@ -213,6 +213,80 @@ imdp_status imdp_value_iteration(imdp_model* m, const imdp_spec* spec, double* V
   return s;
 }
 
+imdp_status imdp_value_iteration_polished(imdp_model* m32, imdp_model* m64, const imdp_spec* spec,
+                                          const imdp_launch_config* cfg32, const imdp_launch_config* cfg64,
+                                          double* V_out, int32_t* k32_out, int32_t* k_out, double* residual_out,
+                                          int32_t* policy_out, void* stream) {
+  set_error("");
+  if (!m32 || !m64 || !spec || !V_out) { set_error("NULL model, spec or V_out"); return IMDP_EINVAL; }
+  if (m32->dev->dtype != IMDP_F32 || m64->dev->dtype != IMDP_F64) {
+    set_error("polishing takes the 32-bit model first and the 64-bit model of the same IMDP second");
+    return IMDP_EINVAL;
+  }
+  const DevModel* a = m32->dev;
+  const DevModel* b = m64->dev;
+  if (m32->device != m64->device || a->n_states != b->n_states || a->n_cols != b->n_cols || a->nnz != b->nnz ||
+      a->h_stateptr != b->h_stateptr || a->h_colptr != b->h_colptr) {
+    set_error("the two models must have the same structure and live on one device");
+    return IMDP_EINVAL;
+  }
+  if (is_slice(a) || is_slice(b)) { set_error("state slices stop on the residual of every slice"); return IMDP_EINVAL; }
+  if (!spec->infinite_time) { set_error("polishing needs an infinite horizon"); return IMDP_EINVAL; }
+  if (!have_device()) { set_error("no CUDA device"); return IMDP_EDEVICE; }
+  DeviceGuard g(m32->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  // 1. 32-bit storage to its own fixed point
+  Session* S32 = nullptr;
+  imdp_status r = Session::create({m32->dev}, {spec}, nullptr, st, &S32);
+  if (r != IMDP_OK) return r;
+  if (cfg32) {
+    imdp_session h{S32};
+    r = imdp_session_set_launch(&h, cfg32, stream);
+    if (r != IMDP_OK) { delete S32; return r; }
+  }
+  std::vector<IterState> its;
+  r = S32->run(32, st);
+  if (r == IMDP_OK) r = S32->read_states(its, st);
+  if (r != IMDP_OK) { delete S32; return r; }
+  const int32_t k32 = its[0].done ? its[0].k_final : its[0].iter;
+  // 2. the 64-bit operator from that iterate: V_k32 and the threshold hints
+  // (entry indices, the same in both storages) move over, and the problem
+  // resumes at iteration k32 until its own residual test passes
+  const int32_t want = policy_out ? 1 : 0;
+  Session* S64 = nullptr;
+  r = Session::create({m64->dev}, {spec}, &want, st, &S64);
+  if (r != IMDP_OK) { delete S32; return r; }
+  if (cfg64) {
+    imdp_session h{S64};
+    r = imdp_session_set_launch(&h, cfg64, stream);
+    if (r != IMDP_OK) { delete S32; delete S64; return r; }
+  }
+  const Problem& P32 = S32->probs_h[0];
+  const Problem& P64 = S64->probs_h[0];
+  IterState it;
+  std::memset(&it, 0, sizeof(it));
+  it.iter = k32;
+  if (k32 >= P64.horizon) {  // the 32-bit phase used every iteration the cap allows
+    it.done = 1;
+    it.k_final = k32;
+    it.noconv = 1;
+  }
+  cudaError_t e = cudaMemcpyAsync(P64.V[k32 & 1], P32.V[k32 & 1], sizeof(uint64_t) * (size_t)P64.n_states,
+                                  cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(P64.hint, P32.hint, sizeof(int32_t) * padded_i32((size_t)b->n_cols), cudaMemcpyDeviceToDevice,
+                        st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S64->its, &it, sizeof(it), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // `it` lives on this stack frame
+  delete S32;
+  if (e != cudaSuccess) { delete S64; return cuda_status(e, "polishing"); }
+  r = S64->run(32, st);
+  if (r == IMDP_OK) r = S64->read(0, V_out, k_out, residual_out, policy_out, st);
+  delete S64;
+  if (r == IMDP_OK && k32_out) *k32_out = k32;
+  return r;
+}
+
 imdp_status imdp_value_iteration_batch(imdp_model* const* models, const imdp_spec* specs, int32_t count,
                                        double* const* V_out, int32_t* k_out, void* stream) {
   set_error("");

@@ -109,3 +109,37 @@ def test_f32_pendulum_batch_k200_within_1e6():
     err = float(np.max(np.abs(V - oV)))
     assert K * model.error_bound() <= 1e-6 + 1e-12
     assert err <= K * model.error_bound() + TOL_F64
+
+
+@pytest.mark.parametrize("prop", ["reach", "reward", "reach_slice"])
+def test_infinite_horizon_polished_in_64_bit(prop):
+    # 32-bit storage to its fixed point, then 64-bit sweeps from there: the
+    # result passes the 64-bit path's own stopping test, needs fewer 64-bit
+    # sweeps than the 64-bit path alone, and sits within the stopping
+    # tolerance of it and of the oracle (binary64)
+    m = banded_imdp(800, 2, 800 * 2 * 40 + 800 * 2 + 1, eps=0.1, seed=56)
+    m32, m64 = _f32(m), g.create_model(m)
+    launch = dict(kernel=g.KERNEL_SLICE) if prop == "reach_slice" else None
+    if prop.startswith("reach"):
+        kw = dict(infinite_time=True, eps=1e-9, horizon=100000, reach=m.goal)
+    else:
+        kw = dict(property=g.IMDP_REWARD, infinite_time=True, eps=1e-9, horizon=100000,
+                  reward=np.linspace(0.0, 1.0, m.n_states), discount=0.95)
+    spec = g.make_spec(**kw)
+    V, k, res = np.zeros(m.n_states), [0], np.zeros(m.n_states)
+    st, k32 = g.imdp_value_iteration_polished(m32, m64, spec, V, k, res, launch32=launch, launch64=launch)
+    assert st == g.IMDP_OK and 0 < k32 < k[0]
+    _, V64, k64, res64, _ = g.value_iteration(m64, m.n_states, **kw)
+    assert k[0] - k32 < k64  # fewer 64-bit sweeps than the 64-bit path alone
+    assert float(np.max(res)) < 1e-9 * max(1.0, float(np.max(np.abs(V64))))  # the 64-bit stopping test held
+    _, oV, _, _, _ = run_oracle(m, **kw)
+    scale = max(1.0, float(np.max(np.abs(oV))))
+    assert float(np.max(np.abs(V - V64))) <= 1e-6 * scale
+    assert float(np.max(np.abs(V - oV))) <= 1e-6 * scale
+    # wrong arguments: storage types swapped, a finite horizon
+    with pytest.raises(g.ImdpError):
+        g.imdp_value_iteration_polished(m64, m32, spec, V)
+    with pytest.raises(g.ImdpError):
+        g.imdp_value_iteration_polished(m32, m64, g.make_spec(horizon=10, reach=m.goal), V)
+    m32.close()
+    m64.close()
