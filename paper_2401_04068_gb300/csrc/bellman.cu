@@ -417,36 +417,49 @@ struct SharedV {
 // and contribute zero. With `carry` the per-lane gap sums count their wraps and
 // saturate; without it the column is narrow (all its gaps add up to < 2^64), so
 // no sum can wrap.
+// Trips of a warm pass from global memory whose loads are in flight ahead of
+// the gather being consumed (three measured no faster on 64-bit storage and
+// slower on 32-bit, whose deeper unroll then runs short of registers).
+constexpr int kPipe = 2;
+
 template <bool carry, bool f32, int gmem, class VP>
 __device__ __forceinline__ void warm_pass(const typename RowsOf<gmem>::type rows, const Bounds<f32, gmem> lg, int32_t k,
                                           const VP V, uint64_t vk, bool pess, int lane,
                                           uint64_t& acc, uint64_t& flt, uint64_t& geq) {
   uint32_t fc = 0, gc = 0;
   const int nb = (k + 31) >> 5;
-  // from global memory the loop is software-pipelined: the next trip's
-  // destination and bounds are requested before this trip's gather (from
-  // shared memory, where the loads are short, the plain loop is faster)
+  // from global memory the loop is software-pipelined kPipe trips deep: the
+  // destinations and bounds of the next trips are requested before this
+  // trip's gather (from shared memory, where the loads are short, the plain
+  // loop is faster)
   constexpr bool pipe = gmem != 0;
   int idx = lane;
-  int32_t r = 0;
-  ulonglong2 b = make_ulonglong2(0, 0);
-  if (pipe) {
-    r = row_if(rows, idx, idx < k);
-    b = lg.at_if(idx, idx < k);
+  int32_t rq[kPipe];
+  ulonglong2 bq[kPipe];
+#pragma unroll
+  for (int d = 0; d < kPipe; ++d) {
+    rq[d] = pipe ? row_if(rows, idx + 32 * d, idx + 32 * d < k) : 0;
+    bq[d] = pipe ? lg.at_if(idx + 32 * d, idx + 32 * d < k) : make_ulonglong2(0, 0);
   }
 #pragma unroll 2
   for (int it = 0; it < nb; ++it) {
     if (!pipe) {
-      r = row_if(rows, idx, idx < k);
-      b = lg.at_if(idx, idx < k);
+      rq[0] = row_if(rows, idx, idx < k);
+      bq[0] = lg.at_if(idx, idx < k);
     }
+    const int32_t r = rq[0];
+    const ulonglong2 b = bq[0];
     const uint64_t v = V.at(r);
     idx += 32;
-    int32_t rn = 0;
-    ulonglong2 bn = make_ulonglong2(0, 0);
     if (pipe) {
-      rn = row_if(rows, idx, idx < k);
-      bn = lg.at_if(idx, idx < k);
+#pragma unroll
+      for (int d = 0; d + 1 < kPipe; ++d) {
+        rq[d] = rq[d + 1];
+        bq[d] = bq[d + 1];
+      }
+      const int nx = idx + 32 * (kPipe - 1);
+      rq[kPipe - 1] = row_if(rows, nx, nx < k);
+      bq[kPipe - 1] = lg.at_if(nx, nx < k);
     }
     const bool below = pess ? (v < vk) : (v > vk);
     acc += __umul64hi(v, b.x + (below ? b.y : 0ull));
@@ -456,10 +469,6 @@ __device__ __forceinline__ void warm_pass(const typename RowsOf<gmem>::type rows
     if (carry) {
       fc += flt < gb ? 1u : 0u;
       gc += geq < ge ? 1u : 0u;
-    }
-    if (pipe) {
-      r = rn;
-      b = bn;
     }
   }
   if (carry) {
@@ -501,21 +510,32 @@ __device__ __forceinline__ void warm_pass32(const typename RowsOf<gmem>::type ro
   }
   // global memory: software-pipelined as in warm_pass
   int idx = lane;
-  int32_t r = row_if(rows, idx, idx < k);
-  uint2 b = ld_stream_u32x2_if(m + idx, idx < k);
+  int32_t rq[kPipe];
+  uint2 bq[kPipe];
+#pragma unroll
+  for (int d = 0; d < kPipe; ++d) {
+    rq[d] = row_if(rows, idx + 32 * d, idx + 32 * d < k);
+    bq[d] = ld_stream_u32x2_if(m + idx + 32 * d, idx + 32 * d < k);
+  }
 #pragma unroll 4
   for (int it = 0; it < nb; ++it) {
+    const int32_t r = rq[0];
+    const uint2 b = bq[0];
     const uint32_t v = V.hi(r);
     idx += 32;
-    const int32_t rn = row_if(rows, idx, idx < k);
-    const uint2 bn = ld_stream_u32x2_if(m + idx, idx < k);
+#pragma unroll
+    for (int d = 0; d + 1 < kPipe; ++d) {
+      rq[d] = rq[d + 1];
+      bq[d] = bq[d + 1];
+    }
+    const int nx = idx + 32 * (kPipe - 1);
+    rq[kPipe - 1] = row_if(rows, nx, nx < k);
+    bq[kPipe - 1] = ld_stream_u32x2_if(m + nx, nx < k);
     const bool below = pess ? (v < vk) : (v > vk);
     const uint32_t g = below ? b.y : 0u;
     acc += ((uint64_t)v * (uint64_t)(b.x + g)) >> s;
     flt += g;
     geq += v == vk ? b.y : 0u;
-    r = rn;
-    b = bn;
   }
 }
 
