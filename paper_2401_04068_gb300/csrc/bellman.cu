@@ -1413,7 +1413,10 @@ __global__ void __launch_bounds__(32 * NW, MINB) bellman_direct_kernel(StepLaunc
 // Trips are taken kLaneGroup at a time and software-pipelined: the next
 // group's destination and bound loads are issued before this group's gathers
 // and arithmetic, so each lane keeps two groups of streamed loads in flight.
-// (Groups of eight trips on 32-bit storage measured no faster and spill more.)
+// (Groups of eight trips on 32-bit storage measured no faster and spill more.
+// The 32-bit pass, whose trips take half the registers, also issues the next
+// group's gathers before this group's arithmetic; the same third stage on
+// 64-bit storage spills.)
 constexpr int kLaneGroup = 4;
 template <bool carry>
 __device__ __forceinline__ void lane_pass64(const int32_t* rows, const ulonglong2* lg, int32_t len, int32_t k,
@@ -1467,37 +1470,54 @@ __device__ __forceinline__ void lane_pass64(const int32_t* rows, const ulonglong
 __device__ __forceinline__ void lane_pass32(const int32_t* rows, const uint2* m, int32_t len, int32_t k,
                                             const uint64_t* __restrict__ V, uint32_t vk, int s, bool pess,
                                             uint64_t& acc, uint64_t& flt, uint64_t& geq) {
-  int32_t r[kLaneGroup];
-  uint2 b[kLaneGroup];
+  // three stages in flight: destinations and bounds of group t0 + 2G, the
+  // gathers of group t0 + G, the arithmetic of group t0 (G = kLaneGroup)
+  constexpr int G = kLaneGroup;
+  int32_t r1[G];
+  uint2 b0[G], b1[G];
+  uint32_t v0[G];
+  {
+    int32_t r0[G];
 #pragma unroll
-  for (int u = 0; u < kLaneGroup; ++u) {
-    r[u] = ld_stream_i32_if(rows + (size_t)u * kSliceStride, u < k);
-    b[u] = ld_stream_u32x2_if(m + (size_t)u * kSliceStride, u < k);
+    for (int u = 0; u < G; ++u) {
+      r0[u] = ld_stream_i32_if(rows + (size_t)u * kSliceStride, u < k);
+      b0[u] = ld_stream_u32x2_if(m + (size_t)u * kSliceStride, u < k);
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u) v0[u] = ld_value_hi_if(V + r0[u], u < k);
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int32_t t = G + u;
+      r1[u] = ld_stream_i32_if(rows + (size_t)t * kSliceStride, t < k);
+      b1[u] = ld_stream_u32x2_if(m + (size_t)t * kSliceStride, t < k);
+    }
   }
-  for (int32_t t0 = 0; t0 < len; t0 += kLaneGroup) {
-    uint32_t v[kLaneGroup];
+  for (int32_t t0 = 0; t0 < len; t0 += G) {
+    uint32_t vn[G];
 #pragma unroll
-    for (int u = 0; u < kLaneGroup; ++u) v[u] = ld_value_hi_if(V + r[u], t0 + u < k);
-    int32_t rn[kLaneGroup];
-    uint2 bn[kLaneGroup];
+    for (int u = 0; u < G; ++u) vn[u] = ld_value_hi_if(V + r1[u], t0 + G + u < k);
+    int32_t r2[G];
+    uint2 b2[G];
 #pragma unroll
-    for (int u = 0; u < kLaneGroup; ++u) {
-      const int32_t t = t0 + kLaneGroup + u;
-      rn[u] = ld_stream_i32_if(rows + (size_t)t * kSliceStride, t < k);
-      bn[u] = ld_stream_u32x2_if(m + (size_t)t * kSliceStride, t < k);
+    for (int u = 0; u < G; ++u) {
+      const int32_t t = t0 + 2 * G + u;
+      r2[u] = ld_stream_i32_if(rows + (size_t)t * kSliceStride, t < k);
+      b2[u] = ld_stream_u32x2_if(m + (size_t)t * kSliceStride, t < k);
     }
 #pragma unroll
-    for (int u = 0; u < kLaneGroup; ++u) {
-      const bool below = pess ? (v[u] < vk) : (v[u] > vk);
-      const uint32_t g = below ? b[u].y : 0u;
-      acc += ((uint64_t)v[u] * (uint64_t)(b[u].x + g)) >> s;
+    for (int u = 0; u < G; ++u) {
+      const bool below = pess ? (v0[u] < vk) : (v0[u] > vk);
+      const uint32_t g = below ? b0[u].y : 0u;
+      acc += ((uint64_t)v0[u] * (uint64_t)(b0[u].x + g)) >> s;
       flt += g;
-      geq += v[u] == vk ? b[u].y : 0u;
+      geq += v0[u] == vk ? b0[u].y : 0u;
     }
 #pragma unroll
-    for (int u = 0; u < kLaneGroup; ++u) {
-      r[u] = rn[u];
-      b[u] = bn[u];
+    for (int u = 0; u < G; ++u) {
+      v0[u] = vn[u];
+      b0[u] = b1[u];
+      r1[u] = r2[u];
+      b1[u] = b2[u];
     }
   }
 }
