@@ -441,15 +441,16 @@ __device__ __forceinline__ void warm_pass(const typename RowsOf<gmem>::type rows
     rq[d] = pipe ? row_if(rows, idx + 32 * d, idx + 32 * d < k) : 0;
     bq[d] = pipe ? lg.at_if(idx + 32 * d, idx + 32 * d < k) : make_ulonglong2(0, 0);
   }
+  // the gather of the next trip is issued before this trip's arithmetic
+  uint64_t vnext = pipe ? V.at(rq[0]) : 0ull;
 #pragma unroll 2
   for (int it = 0; it < nb; ++it) {
     if (!pipe) {
       rq[0] = row_if(rows, idx, idx < k);
       bq[0] = lg.at_if(idx, idx < k);
     }
-    const int32_t r = rq[0];
     const ulonglong2 b = bq[0];
-    const uint64_t v = V.at(r);
+    const uint64_t v = pipe ? vnext : V.at(rq[0]);
     idx += 32;
     if (pipe) {
 #pragma unroll
@@ -460,6 +461,7 @@ __device__ __forceinline__ void warm_pass(const typename RowsOf<gmem>::type rows
       const int nx = idx + 32 * (kPipe - 1);
       rq[kPipe - 1] = row_if(rows, nx, nx < k);
       bq[kPipe - 1] = lg.at_if(nx, nx < k);
+      vnext = V.at(rq[0]);
     }
     const bool below = pess ? (v < vk) : (v > vk);
     acc += __umul64hi(v, b.x + (below ? b.y : 0ull));
@@ -517,11 +519,11 @@ __device__ __forceinline__ void warm_pass32(const typename RowsOf<gmem>::type ro
     rq[d] = row_if(rows, idx + 32 * d, idx + 32 * d < k);
     bq[d] = ld_stream_u32x2_if(m + idx + 32 * d, idx + 32 * d < k);
   }
+  uint32_t vnext = V.hi(rq[0]);
 #pragma unroll 4
   for (int it = 0; it < nb; ++it) {
-    const int32_t r = rq[0];
     const uint2 b = bq[0];
-    const uint32_t v = V.hi(r);
+    const uint32_t v = vnext;
     idx += 32;
 #pragma unroll
     for (int d = 0; d + 1 < kPipe; ++d) {
@@ -531,6 +533,7 @@ __device__ __forceinline__ void warm_pass32(const typename RowsOf<gmem>::type ro
     const int nx = idx + 32 * (kPipe - 1);
     rq[kPipe - 1] = row_if(rows, nx, nx < k);
     bq[kPipe - 1] = ld_stream_u32x2_if(m + nx, nx < k);
+    vnext = V.hi(rq[0]);
     const bool below = pess ? (v < vk) : (v > vk);
     const uint32_t g = below ? b.y : 0u;
     acc += ((uint64_t)v * (uint64_t)(b.x + g)) >> s;
