@@ -291,8 +291,17 @@ IMDP_API void imdp_session_destroy(imdp_session* s);
  * Launch configuration of a session's Bellman step (no counterpart in the
  * paper, whose GPU kernels have one fixed shape). Every configuration computes
  * the same words; they differ in speed only. Zero fields mean "by rule".
- *   kernel        0 by rule (the single-CTA kernel for a session of one small
- *                 problem, else ring); 1 ring: a producer warp bulk-copies tiles of
+ *   kernel        0 by rule: the single-CTA kernel for a session of one small
+ *                 problem; else, from the shape of the session's problems (the
+ *                 autotuner's choices on GB300 for the benchmark shapes), direct
+ *                 with 3 CTAs per SM and 1024-entry tiles when their columns hold
+ *                 256 or more transitions on average, otherwise slice with 3 CTAs
+ *                 per SM (4 when every problem has 32-bit storage) when every
+ *                 model already has its slice layout (see 4 below: building it
+ *                 costs about as many iterations' time as a few hundred save),
+ *                 otherwise ring (the server's rule is the single-CTA kernel or
+ *                 ring);
+ *                 1 ring: a producer warp bulk-copies tiles of
  *                 consecutive states into a three-stage shared-memory ring for
  *                 consumer warps; 2 direct: every warp takes the next tile and
  *                 streams its columns from global memory itself; 3 single CTA:
@@ -311,9 +320,11 @@ IMDP_API void imdp_session_destroy(imdp_session* s);
  *   cta_warps     ring: 16 or 24 warps per CTA (24 only without wide states; rule:
  *                 24 when the tiles hold 16 or more columns on average); direct
  *                 and slice: 8
- *   ctas_per_sm   direct and slice: 3 or 4 (rule 4); ring: 1
+ *   ctas_per_sm   direct and slice: 3 or 4 (rule 4 for an explicit kernel, else
+ *                 as above); ring: 1
  *   tile_entries  tile plan: at most this many transitions per tile, 1..3072
- *                 (rule 3072; a single state may exceed a smaller limit; the
+ *                 (rule 3072, 1024 for the direct kernel by rule; a single
+ *                 state may exceed a smaller limit; the
  *                 slice kernel has no tile plan and ignores it)
  *   wide_col      a state with a column of this many transitions or more (or
  *                 more than 3072 transitions in all) runs in the block-wide

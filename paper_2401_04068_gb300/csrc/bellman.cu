@@ -2432,6 +2432,11 @@ LaunchConfig resolve_launch(const StepLaunch& L, const LaunchConfig* cfg) {
     }
     r.kernel = kKernelRule;
   }
+  if (r.kernel == kKernelRule && L.shape_rule) {
+    r.kernel = L.shape_rule;
+    if (r.ctas_per_sm <= 0) r.ctas_per_sm = (r.kernel == kKernelSlice && L.shape_f32) ? 4 : 3;
+    if (r.kernel == kKernelDirect && r.tile_entries <= 0) r.tile_entries = kRuleDirectTile;
+  }
   if (r.kernel == kKernelSlice) {
     r.cta_warps = kSliceWarps;
     r.ctas_per_sm = r.ctas_per_sm == 3 ? 3 : 4;

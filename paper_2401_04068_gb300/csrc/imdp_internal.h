@@ -182,6 +182,14 @@ enum : int32_t { kKernelRule = 0, kKernelRing = 1, kKernelDirect = 2, kKernelTin
 // A session of one problem this small runs all its iterations in one launch of
 // one CTA, with the model and values in shared memory (bellman_tiny_kernel).
 constexpr int32_t kTinyMaxStates = 1024, kTinyMaxCols = 1024, kTinyMaxEntries = 4096;
+// The rule for a session's shape (the choices the autotuner makes on GB300 for
+// the benchmark shapes): problems whose columns hold kRuleLongColumn entries or
+// more on average run the direct kernel (3 CTAs per SM, kRuleDirectTile-entry
+// tiles); shorter columns run the slice kernel (3 CTAs per SM on 64-bit
+// storage, 4 on 32-bit) when the device has room for its second copy of the
+// models, else the ring kernel.
+constexpr int64_t kRuleLongColumn = 256;
+constexpr int32_t kRuleDirectTile = 1024;
 constexpr int kDirectWarps = 8;  // warps per CTA of the direct kernel
 constexpr int kSliceWarps = 8;   // warps per CTA of the slice kernel
 struct LaunchConfig {
@@ -230,6 +238,11 @@ struct StepLaunch {
   // with r the largest rank still running.
   const int32_t* rank_of;        // count: rank of each problem
   const int32_t* rank_tile_end;  // count: tiles of ranks 0..r
+  // the kernel "by rule" stands for when the single-CTA kernel does not apply
+  // (0: the ring kernel; a session sets it from its problems' shape, see
+  // kRuleLongColumn) and whether every problem has 32-bit storage
+  int32_t shape_rule;
+  int32_t shape_f32;
   int32_t tiny_ok;     // one small problem (sizes below): the single-CTA kernel may run it
   int32_t tiny_states, tiny_cols, tiny_entries;
   // slice kernel: the work items (tile = window, slice of the model's layout) in

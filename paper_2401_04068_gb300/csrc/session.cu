@@ -165,9 +165,6 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
     return ka > kb;
   });
   S->fixed_h = fixed;
-  std::vector<Tile> tiles;
-  std::vector<int2> wide;
-  S->build_plan(S->cfg, tiles, wide);
   S->rank_of = S->alloc<int32_t>(count);
   S->rank_tile_end = S->alloc<int32_t>(count);
   // each problem's hint block starts on a 16-byte boundary and is padded, so
@@ -275,8 +272,34 @@ imdp_status Session::create(const std::vector<DevModel*>& ms, const std::vector<
     S->L.tiny_cols = ms[0]->n_cols;
     S->L.tiny_entries = (int32_t)ms[0]->nnz;
   }
+  // the kernel by rule for this batch's shape: long columns (the mean over
+  // all problems) the direct kernel; short ones the slice kernel when every
+  // model already carries its slice layout (building one costs about as much as
+  // 450 iterations of the slice kernel save on the pendulum shape), else ring
+  {
+    int64_t nnz = 0, cols = 0;
+    bool all32 = true, laid_out = true;
+    for (DevModel* m : ms) {
+      nnz += m->nnz;
+      cols += m->n_cols;
+      all32 = all32 && m->lg32 != nullptr;
+      std::lock_guard<std::mutex> lk(m->slices_mu);
+      laid_out = laid_out && m->slices != nullptr;
+    }
+    if (nnz >= kRuleLongColumn * std::max<int64_t>(cols, 1))
+      S->L.shape_rule = kKernelDirect;
+    else if (laid_out)
+      S->L.shape_rule = kKernelSlice;
+    S->L.shape_f32 = all32 ? 1 : 0;
+  }
   S->grid = bellman_grid();
-  imdp_status r = S->install_plan(tiles, wide, st);
+  const bool slice = resolve_launch(S->L, &S->cfg).kernel == kKernelSlice;
+  imdp_status r = slice ? S->prepare_slices(st) : IMDP_OK;
+  if (r != IMDP_OK) { delete S; return r; }
+  std::vector<Tile> tiles;
+  std::vector<int2> wide;
+  S->build_plan(S->cfg, tiles, wide);
+  r = S->install_plan(tiles, wide, st, slice);
   if (r != IMDP_OK) { delete S; return r; }
   r = S->reset(st);
   if (r != IMDP_OK) { delete S; return r; }

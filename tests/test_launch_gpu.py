@@ -319,3 +319,54 @@ def test_slice_kernel_windows_switching_and_policy(dtype):
                 assert np.array_equal(pa, pb)
     for x in models:
         x.close()
+
+
+def test_rule_follows_the_batch_shape():
+    # By rule (no launch configuration) a session runs the kernel the
+    # autotuner picks on GB300 for its shape: long columns the direct kernel
+    # (3 CTAs per SM, 1024-entry tiles); short columns the ring kernel while a
+    # model has no slice layout, the slice kernel once it has one. The words
+    # are those of any other configuration.
+    K = 25
+    long_m = banded_imdp(300, 2, 300 * 2 * 300 + 300 * 2 + 1, eps=0.05, seed=81)
+    short_m = banded_imdp(2000, 1, 2000 * 40 + 2000 + 1, eps=0.05, seed=82)
+    assert long_m.nnz >= 256 * long_m.n_cols and short_m.nnz < 256 * short_m.n_cols
+
+    def by_rule(model, m):
+        sess = g.imdp_session_create([model], [g.make_spec(horizon=K, reach=m.goal)])
+        got = g.imdp_session_get_launch(sess)
+        g.imdp_session_step(sess, K)
+        raw, k = g.imdp_session_checkpoint(sess, 0)
+        sess.close()
+        assert k == K
+        return got, raw
+
+    def explicit(model, m, cfg):
+        sess = g.imdp_session_create([model], [g.make_spec(horizon=K, reach=m.goal)])
+        g.imdp_session_set_launch(sess, **cfg)
+        g.imdp_session_step(sess, K)
+        raw, _ = g.imdp_session_checkpoint(sess, 0)
+        sess.close()
+        return raw
+
+    mdl = g.create_model(long_m)
+    got, raw = by_rule(mdl, long_m)
+    assert (got["kernel"], got["ctas_per_sm"], got["tile_entries"]) == (g.KERNEL_DIRECT, 3, 1024)
+    np.testing.assert_array_equal(raw, explicit(mdl, long_m, dict(kernel=g.KERNEL_RING, cta_warps=16)))
+    mdl.close()
+
+    mdl = g.create_model(short_m)
+    got, raw = by_rule(mdl, short_m)
+    assert got["kernel"] == g.KERNEL_RING
+    # a session that selects the slice kernel builds the model's slice layout
+    raw_slice = explicit(mdl, short_m, dict(kernel=g.KERNEL_SLICE))
+    got2, raw2 = by_rule(mdl, short_m)
+    assert (got2["kernel"], got2["ctas_per_sm"]) == (g.KERNEL_SLICE, 3)
+    np.testing.assert_array_equal(raw, raw_slice)
+    np.testing.assert_array_equal(raw, raw2)
+    _, oV, _, _, _ = run_oracle(short_m, horizon=K, reach=short_m.goal)
+    # the one-shot call runs by rule too (now the slice kernel)
+    st, V, k, _, _ = g.value_iteration(mdl, short_m.n_states, horizon=K, reach=short_m.goal)
+    assert st == "ok" and k == K
+    np.testing.assert_allclose(V, oV, rtol=0, atol=TOL_F64)
+    mdl.close()
